@@ -1,0 +1,618 @@
+"""Plain, slow FP64 CPU oracle of the paper's method (arXiv 2510.11508).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the CPU-baseline / reference legs of ``bench.py``; the product path
+(the CUDA library and its Python binding) never imports, links or runs it.
+
+It follows the method's steps in the paper's order (Algorithm 1 of the
+supplementary "Pseudocode of our method"), in float64, with scipy.sparse
+matrices and its direct sparse solves of the normal equations.  Library primitives used as
+steps: sparse matrix products, ``scipy.sparse.csgraph.connected_components``,
+``numpy`` sorts and reductions.  Nothing is blocked, fused or reordered beyond
+what the equations state: every system is assembled row by row exactly as the
+paper writes its design matrices, and solved through the normal equations.
+
+Notation (the paper's):
+    z~    log-depth per valid pixel (linear depth for the orthographic reading)
+    w~    omega~_{b->a}, the model-of-continuity coefficient of a directed edge
+    chi   residual z~_a - z~_b - w~_{b->a}
+    pi    pixel -> component map of the current partition
+    s~    per-component log-scale
+
+Readings of passages the paper leaves open are marked "Reading:" where used.
+Parity status of each function is stated in its docstring; the pins live in
+tests/test_oracle_pins.py.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional
+
+import numpy as np
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+ORTHO = 0
+PERSP = 1
+RIGHT = 0
+DOWN = 1
+
+
+@dataclasses.dataclass
+class Camera:
+    camera: int = PERSP
+    fx: float = 1.0
+    fy: float = 1.0
+    cx: float = 0.0
+    cy: float = 0.0
+
+    @staticmethod
+    def from_dict(d):
+        return Camera(int(d["camera"]), float(d["fx"]), float(d["fy"]), float(d["cx"]), float(d["cy"]))
+
+
+@dataclasses.dataclass
+class Params:
+    """Algorithm 1 inputs (theta_c, can merge, freq_merging, dE_max, T) plus the
+    hyper-parameters of the weights (k of the BiNI sigmoid, L and U of the
+    outlier reweighting) and the solver tolerances.  theta_c_deg=None is the
+    paper's single-pixel limit (every pixel its own component)."""
+    theta_c_deg: Optional[float] = 3.5
+    k: float = 2.0
+    L: float = 1e-5
+    U: float = 1e-3
+    T: int = 15
+    dE_max: float = 1e-3
+    can_merge: bool = False
+    freq_merging: int = 5
+    n_fill_irls: int = 1
+    hard_outliers: bool = False
+
+    @staticmethod
+    def from_dict(d):
+        p = Params()
+        for k_, v_ in d.items():
+            if hasattr(p, k_):
+                setattr(p, k_, v_)
+        return p
+
+
+# ---------------------------------------------------------------------------
+# geometry: rays, edges, model of continuity (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def rays(H: int, W: int, cam: Camera) -> np.ndarray:
+    """Ray direction tau(u, v) per pixel, [H*W, 3].
+
+    Reading (Sec. 3.1, Eq. 3 names tau only as "ray direction vectors"): for the
+    pinhole camera of Eq. 2, tau(u, v) = ((u - c_x)/f_x, (v - c_y)/f_y, 1) with
+    u the column and v the row, so that the 3D point is z * tau and z is the depth
+    along the optical axis.  Orthographic reading: tau = (0, 0, 1).
+    """
+    v, u = np.mgrid[0:H, 0:W].astype(np.float64)
+    if cam.camera == PERSP:
+        t = np.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, np.ones_like(u)], -1)
+    else:
+        t = np.stack([np.zeros_like(u), np.zeros_like(u), np.ones_like(u)], -1)
+    return t.reshape(-1, 3)
+
+
+def edge_list(mask: np.ndarray):
+    """All edges of the pixel graph G_0 = (V, E) with 4-connectivity (Sec. 3.2):
+    pairs (a, b) of valid neighbouring pixels, b the right (dir 0) or lower
+    (dir 1) neighbour of a.  Edges are returned sorted by the edge id
+    2 * a + dir."""
+    H, W = mask.shape
+    m = mask.reshape(-1).astype(bool)
+    idx = np.arange(H * W, dtype=np.int64)
+    u = idx % W
+    v = idx // W
+    ra = idx[(u < W - 1) & m]
+    ra = ra[m[ra + 1]]
+    da = idx[(v < H - 1) & m]
+    da = da[m[da + W]]
+    a = np.concatenate([ra, da])
+    d = np.concatenate([np.zeros(len(ra), np.int64), np.ones(len(da), np.int64)])
+    b = np.where(d == RIGHT, a + 1, a + W)
+    order = np.argsort(2 * a + d, kind="stable")
+    return a[order], b[order], d[order]
+
+
+def _normals64(normals: np.ndarray) -> np.ndarray:
+    n = np.asarray(normals)
+    return n.reshape(-1, n.shape[-1])[:, :3].astype(np.float64)
+
+
+def omega(normals, cam: Camera, H: int, W: int, a, b, d) -> np.ndarray:
+    """Coefficient w~_{b->a} of the model of continuity for each edge.
+
+    Perspective: Eq. 3 (the model of Milano et al. the paper adopts),
+        w~_{b->a} = log( (n_a.tau_m * n_b.tau_b) / (n_a.tau_a * n_b.tau_m) ),
+    with m the midpoint of a and b (Reading: "a subpixel that interpolates
+    between a and b" is the midpoint).  Reading: the logarithm is taken of the
+    absolute value of the ratio (it is positive for any surface seen from both
+    rays), each product clamped below at 1e-300.
+
+    Orthographic (Reading: the paper treats central cameras only): the same
+    tangent-plane construction with parallel rays in linear depth gives
+    z_a - z_b = (n_ax/n_az + n_bx/n_bz) / 2 for b right of a, and the same with
+    n_y for b below a.
+
+    Pinned: exact on planes (closed form) and O(h^2) on a sphere.
+    """
+    n = _normals64(normals)
+    if cam.camera == PERSP:
+        tau = rays(H, W, cam)
+        ua, va = (a % W).astype(np.float64), (a // W).astype(np.float64)
+        ub, vb = (b % W).astype(np.float64), (b // W).astype(np.float64)
+        um, vm = 0.5 * (ua + ub), 0.5 * (va + vb)
+        tm = np.stack([(um - cam.cx) / cam.fx, (vm - cam.cy) / cam.fy, np.ones_like(um)], -1)
+        na_tm = np.sum(n[a] * tm, 1)
+        nb_tb = np.sum(n[b] * tau[b], 1)
+        na_ta = np.sum(n[a] * tau[a], 1)
+        nb_tm = np.sum(n[b] * tm, 1)
+        num = np.maximum(np.abs(na_tm * nb_tb), 1e-300)
+        den = np.maximum(np.abs(na_ta * nb_tm), 1e-300)
+        return np.log(num / den)
+    comp = np.where(d == RIGHT, 0, 1)
+    return 0.5 * (n[a, comp] / n[a, 2] + n[b, comp] / n[b, 2])
+
+
+def gamma(normals, cam: Camera, H: int, W: int, p, d) -> np.ndarray:
+    """gamma_{.->p} = f * n_p . tau_p (Sec. 3.1, Eq. 6), the pixel factor of the
+    BiNI weight.  Reading: f = f_x for horizontal edges and f_y for vertical
+    ones, as in Eq. 2; orthographic: f = 1, tau = (0, 0, 1), so gamma = n_pz."""
+    n = _normals64(normals)
+    tau = rays(H, W, cam)
+    nt = np.sum(n[p] * tau[p], 1)
+    if cam.camera == PERSP:
+        return np.where(d == RIGHT, cam.fx, cam.fy) * nt
+    return nt
+
+
+def sigmoid(x, k=1.0):
+    """sigma_k(x) = 1 / (1 + exp(-k x)) (Sec. 3.1, after Eq. 4)."""
+    with np.errstate(over="ignore"):
+        return 1.0 / (1.0 + np.exp(-k * np.asarray(x, np.float64)))
+
+
+def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
+    """Directed BiNI weight W_{b->a} = gamma_{b->a}^2 * w^BiNI_{b->a}
+    (Sec. 3.1, Eqs. 4-5):
+        w^BiNI_{b->a} = sigma_k( gamma^2 ((z~_{-b} - z~_a)^2 - (z~_b - z~_a)^2) ),
+    where -b is a's neighbour on the side opposite to b.
+
+    Reading: when -b is outside the image, invalid, or (during the component
+    fill, `same_component` given) outside a's component, its squared difference
+    is taken as 0.
+    a, b: endpoints with b = a + step(d) or b = a - step(d); the opposite
+    neighbour is a - (b - a).
+    """
+    step = b - a
+    ob = a - step
+    ua, va = a % W, a // W
+    sgn = np.sign(step)
+    du = np.where(d == RIGHT, -sgn, 0)
+    dv = np.where(d == RIGHT, 0, -sgn)
+    uo, vo = ua + du, va + dv
+    inside = (uo >= 0) & (uo < W) & (vo >= 0) & (vo < H)
+    obc = np.where(inside, ob, 0)
+    ok = inside & valid[obc]
+    if same_component is not None:
+        ok &= same_component[obc] == same_component[a]
+    opp = np.where(ok, (zt[obc] - zt[a]) ** 2, 0.0)
+    x = gam * gam * (opp - (zt[b] - zt[a]) ** 2)
+    return gam * gam * sigmoid(x, k)
+
+
+def outlier_weight(chi_abs, L=1e-5, U=1e-3, hard=False):
+    """Soft outlier reweighting W^out (Sec. 3.4, Eq. 11):
+        sigma_1( 4/(L~ - U~) * (2 log10|chi| - (L~ + U~)) ),  ~ = log10,
+    mapping |chi| = U to sigma(-4) and |chi| = L to sigma(4).
+    Reading: |chi| is clamped below at 1e-30, so |chi| = 0 gives weight 1.
+    hard=True is the ablation's hard variant (supplementary): 0 if |chi| >= U,
+    else 1."""
+    x = np.maximum(np.abs(np.asarray(chi_abs, np.float64)), 1e-30)
+    if hard:
+        return (x < U).astype(np.float64)
+    Lt, Ut = math.log10(L), math.log10(U)
+    return sigmoid(4.0 / (Lt - Ut) * (2.0 * np.log10(x) - (Lt + Ut)), 1.0)
+
+
+# ---------------------------------------------------------------------------
+# seeding (Sec. 3.3, first paragraph)
+# ---------------------------------------------------------------------------
+
+def cos_theta(theta_c_deg: float) -> float:
+    """cos(theta_c) evaluated once, as cos(theta_deg * (pi / 180))."""
+    return math.cos(theta_c_deg * (math.pi / 180.0))
+
+
+def seed_edge_keep(normals, a, b, theta_c_deg) -> np.ndarray:
+    """Edge predicate of Sec. 3.3: theta_{a,b} = arccos(n_a . n_b) < theta_c,
+    evaluated as n_a . n_b > cos(theta_c) (arccos is decreasing), with the dot
+    product of the input values summed in float64 in the order x, y, z.
+    theta_c = None keeps no edge (single-pixel components, Sec. 3.2)."""
+    if theta_c_deg is None:
+        return np.zeros(len(a), bool)
+    n = _normals64(normals)
+    dot = n[a, 0] * n[b, 0] + n[a, 1] * n[b, 1]
+    dot = dot + n[a, 2] * n[b, 2]
+    return dot > cos_theta(theta_c_deg)
+
+
+def canonical_labels(n_nodes: int, nodes: np.ndarray, ea, eb):
+    """Connected components of the graph (nodes, edges ea-eb), labelled
+    canonically: a component's label is the rank of its smallest node index
+    among all components' smallest node indices.  Returns (label per node of
+    `nodes`, K).  Reading: the paper leaves the order of pi_m open (Eq. 7)."""
+    if len(nodes) == 0:
+        return np.zeros(0, np.int64), 0
+    pos = np.full(n_nodes, -1, np.int64)
+    pos[nodes] = np.arange(len(nodes))
+    g = sp.coo_matrix((np.ones(len(ea)), (pos[ea], pos[eb])), shape=(len(nodes), len(nodes)))
+    ncc, cc = connected_components(g, directed=False)
+    mins = np.full(ncc, np.iinfo(np.int64).max)
+    np.minimum.at(mins, cc, nodes)
+    rank = np.empty(ncc, np.int64)
+    rank[np.argsort(mins, kind="stable")] = np.arange(ncc)
+    return rank[cc], int(ncc)
+
+
+def seed_components(normals, mask, theta_c_deg):
+    """Initial partition {C_c^(0)}: connected components of the subgraph of G_0
+    that keeps the edges with theta_{a,b} < theta_c (Sec. 3.3).  Returns
+    (labels int64 [H*W], -1 at invalid pixels; K)."""
+    H, W = mask.shape
+    a, b, d = edge_list(mask)
+    keep = seed_edge_keep(normals, a, b, theta_c_deg)
+    valid_idx = np.nonzero(mask.reshape(-1))[0]
+    lab, K = canonical_labels(H * W, valid_idx, a[keep], b[keep])
+    labels = np.full(H * W, -1, np.int64)
+    labels[valid_idx] = lab
+    return labels, K
+
+
+# ---------------------------------------------------------------------------
+# linear algebra helpers
+# ---------------------------------------------------------------------------
+
+def project_zero_mean(x, block, nblocks):
+    """Remove each block's mean (the gauge of a singular Laplacian block)."""
+    cnt = np.bincount(block, None, nblocks)
+    s = np.bincount(block, x, nblocks)
+    mean = np.where(cnt > 0, s / np.maximum(cnt, 1), 0.0)
+    return x - mean[block]
+
+
+def solve_min_norm(M, g):
+    """Minimum-norm solution of the singular normal equations M x = g of a
+    weighted graph Laplacian M (the result cg(M, g) approaches from x = 0).
+
+    Written out as its definition: on each connected block of M's graph
+    (off-diagonal entries != 0) one node is pinned to 0, the remaining
+    nonsingular system is solved by sparse LU (scipy's spsolve), and the block's
+    mean is removed (the null space of a connected Laplacian block is the
+    constants).  Isolated nodes get 0.  Returns x."""
+    from scipy.sparse.linalg import spsolve
+    M = sp.csr_matrix(M)
+    n = M.shape[0]
+    if n == 0:
+        return np.zeros(0)
+    off = M - sp.diags(M.diagonal())
+    off.eliminate_zeros()
+    nb, blk = connected_components(off, directed=False)
+    first = np.full(nb, n, np.int64)
+    np.minimum.at(first, blk, np.arange(n))
+    keep = np.ones(n, bool)
+    keep[first] = False
+    x = np.zeros(n)
+    if keep.any():
+        Mk = M[keep][:, keep].tocsc()
+        x[keep] = spsolve(Mk, np.asarray(g)[keep])
+    return project_zero_mean(x, blk, nb)
+
+
+# ---------------------------------------------------------------------------
+# component fill (Sec. 3.3, Eq. 9-10)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Geometry:
+    H: int
+    W: int
+    valid: np.ndarray    # bool [H*W]
+    a: np.ndarray
+    b: np.ndarray
+    d: np.ndarray
+    omega: np.ndarray    # w~_{b->a} per edge
+    gam_ba: np.ndarray   # gamma_{b->a} = f n_a.tau_a per edge
+    gam_ab: np.ndarray   # gamma_{a->b} = f n_b.tau_b per edge
+
+
+def geometry(normals, mask, cam: Camera) -> Geometry:
+    H, W = mask.shape
+    a, b, d = edge_list(mask)
+    return Geometry(H, W, mask.reshape(-1).astype(bool), a, b, d,
+                    omega(normals, cam, H, W, a, b, d),
+                    gamma(normals, cam, H, W, a, d),
+                    gamma(normals, cam, H, W, b, d))
+
+
+def intra_system(geo: Geometry, labels, zt, k):
+    """A_c, b_c, W_c of Eq. 9 stacked over all components (block diagonal):
+    two rows per intra-component edge (a, b), one per direction,
+        row (b->a): +1 at a, -1 at b, rhs w~_{b->a},         weight W_{b->a}
+        row (a->b): +1 at b, -1 at a, rhs w~_{a->b} = -w~_{b->a}, weight W_{a->b}
+    with W from the BiNI model (Eq. 5) at the current z~ (Reading: -b restricted
+    to a's component)."""
+    n = geo.H * geo.W
+    sel = (labels[geo.a] == labels[geo.b]) & (labels[geo.a] >= 0)
+    a, b, om = geo.a[sel], geo.b[sel], geo.omega[sel]
+    ne = len(a)
+    rows = np.repeat(np.arange(2 * ne), 2)
+    cols = np.empty(4 * ne, np.int64)
+    vals = np.empty(4 * ne)
+    cols[0::4], cols[1::4], cols[2::4], cols[3::4] = a, b, b, a
+    vals[0::4], vals[1::4], vals[2::4], vals[3::4] = 1.0, -1.0, 1.0, -1.0
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(2 * ne, n))
+    rhs = np.empty(2 * ne)
+    rhs[0::2], rhs[1::2] = om, -om
+    w = np.empty(2 * ne)
+    w[0::2] = bini_weight(zt, geo.gam_ba[sel], a, b, geo.d[sel], geo.H, geo.W, geo.valid, k, labels)
+    w[1::2] = bini_weight(zt, geo.gam_ab[sel], b, a, geo.d[sel], geo.H, geo.W, geo.valid, k, labels)
+    return A, rhs, w
+
+
+def fill_components(geo: Geometry, labels, K, k=2.0, n_irls=1):
+    """Fill each component (Sec. 3.3): z~ initialised to 0, then
+    z~_c <- cg(A_c^T W_c A_c, A_c^T W_c b_c) for every component independently
+    (the blocks of one block-diagonal system).  The oracle computes the result
+    CG converges to from z~ = 0, the minimum-norm (zero-mean per component)
+    least-squares solution, directly (`solve_min_norm`).  `n_irls` sweeps
+    recompute W at the current z~; the paper finds one sweep sufficient.
+    Returns (z~ [H*W] with NaN at invalid pixels, number of sweeps)."""
+    n = geo.H * geo.W
+    vidx = np.nonzero(geo.valid)[0]
+    zt = np.zeros(n)
+    blk = labels[vidx]
+    iters = 0
+    for _ in range(max(1, n_irls)):
+        A, rhs, w = intra_system(geo, labels, zt, k)
+        Wd = sp.diags(w)
+        M = (A.T @ Wd @ A).tocsr()[vidx][:, vidx]
+        g = (A.T @ (w * rhs))[vidx]
+        zt[vidx] = project_zero_mean(solve_min_norm(M, g), blk, K)
+        iters += 1
+    out = np.full(n, np.nan)
+    out[vidx] = zt[vidx]
+    return out, iters
+
+
+# ---------------------------------------------------------------------------
+# relative-scale optimisation (Sec. 3.4) and merging (Sec. 3.5)
+# ---------------------------------------------------------------------------
+
+def inter_edges(geo: Geometry, labels):
+    """E_inter^(m) (Eq. 7): edges whose endpoints lie in different components."""
+    return np.nonzero((labels[geo.a] != labels[geo.b]) & (labels[geo.a] >= 0))[0]
+
+
+def residual(geo: Geometry, zt, e):
+    """chi_{b->a} = z~_a - z~_b - w~_{b->a} (Eq. 4) on edges e."""
+    return zt[geo.a[e]] - zt[geo.b[e]] - geo.omega[e]
+
+
+def scale_system(geo: Geometry, labels, K, zt, t, params: Params, e=None):
+    """A_m, b_m (Eq. 13) and W_m^(t) for iteration t.
+
+    Two rows per inter edge (a, b):
+        row (b->a): +1 at pi(a), -1 at pi(b), rhs w~_{b->a} - (z~_a - z~_b)
+        row (a->b): +1 at pi(b), -1 at pi(a), rhs w~_{a->b} - (z~_b - z~_a)
+    Weights: 1 for t <= 1 (alignment, Sec. 3.4); for t > 1 the BiNI weight W
+    (Eq. 5) times W^out (Eq. 11) of |chi^(t-1)|, the residual at the current z~.
+    Reading: z~ inside W is the current z~, and -b may be any valid pixel."""
+    if e is None:
+        e = inter_edges(geo, labels)
+    a, b = geo.a[e], geo.b[e]
+    ne = len(e)
+    rho = zt[a] - zt[b] - geo.omega[e]
+    pa, pb = labels[a], labels[b]
+    rows = np.repeat(np.arange(2 * ne), 2)
+    cols = np.empty(4 * ne, np.int64)
+    vals = np.empty(4 * ne)
+    cols[0::4], cols[1::4], cols[2::4], cols[3::4] = pa, pb, pb, pa
+    vals[0::4], vals[1::4], vals[2::4], vals[3::4] = 1.0, -1.0, 1.0, -1.0
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(2 * ne, K))
+    rhs = np.empty(2 * ne)
+    rhs[0::2], rhs[1::2] = -rho, rho
+    if t <= 1:
+        w = np.ones(2 * ne)
+    else:
+        wo = outlier_weight(np.abs(rho), params.L, params.U, params.hard_outliers)
+        w = np.empty(2 * ne)
+        w[0::2] = bini_weight(zt, geo.gam_ba[e], a, b, geo.d[e], geo.H, geo.W, geo.valid, params.k) * wo
+        w[1::2] = bini_weight(zt, geo.gam_ab[e], b, a, geo.d[e], geo.H, geo.W, geo.valid, params.k) * wo
+    return A, rhs, w, e
+
+
+def quotient_components(K, labels, geo: Geometry, e):
+    """Connected components of Q_m (node -> id)."""
+    pa, pb = labels[geo.a[e]], labels[geo.b[e]]
+    g = sp.coo_matrix((np.ones(len(e)), (pa, pb)), shape=(K, K))
+    ncc, cc = connected_components(g, directed=False)
+    return cc, ncc
+
+
+def solve_scales(A, rhs, w, K, qcc, nq):
+    """s~ <- cg(A^T W A, A^T W b) (Eq. 14) from s~ = 0.  The oracle computes the
+    result CG converges to, the minimum-norm least-squares solution (zero mean
+    over the nodes of each connected component of Q_m), directly."""
+    Wd = sp.diags(w)
+    M = (A.T @ Wd @ A).tocsr()
+    g = A.T @ (w * rhs)
+    s = solve_min_norm(M, g)
+    return project_zero_mean(s, qcc, nq), 1
+
+
+def energy(A, rhs, w, s):
+    """E_t = (A s - b)^T W (A s - b) (Sec. 3.4, last paragraph)."""
+    r = A @ s - rhs
+    return float(np.sum(w * r * r))
+
+
+def merge_labels(labels, K, geo: Geometry, e, chi_abs32):
+    """Merging (Sec. 3.5).  (i) for every node c of Q_m, the incident inter edge
+    with the smallest |chi|; (ii) the subgraph of Q_m with those edges;
+    (iii) its connected components are the new partition.
+
+    Reading (tie-break, left open): edges are compared by the float32 value of
+    |chi| (its bit pattern), then by the edge id 2 * a + dir.  New labels are the
+    ranks of each group's smallest old label (so label order follows the old
+    one).  `chi_abs32` is float32 |chi| per edge in `e`.
+    Returns (new labels [H*W], K_new, selected edge id per old component or -1)."""
+    chi_abs32 = np.asarray(chi_abs32, np.float32)
+    bits = chi_abs32.view(np.uint32).astype(np.uint64)
+    eid = (2 * geo.a[e] + geo.d[e]).astype(np.uint64)
+    key = (bits << np.uint64(32)) | eid
+    best = np.full(K, np.iinfo(np.uint64).max, np.uint64)
+    pa, pb = labels[geo.a[e]], labels[geo.b[e]]
+    np.minimum.at(best, pa, key)
+    np.minimum.at(best, pb, key)
+    has = best != np.iinfo(np.uint64).max
+    sel_eid = np.where(has, (best & np.uint64(0xFFFFFFFF)).astype(np.int64), -1)
+    # endpoints of the selected edges
+    ea = sel_eid[has] // 2
+    ed = sel_eid[has] % 2
+    eb = np.where(ed == RIGHT, ea + 1, ea + geo.W)
+    newlab, Kn = canonical_labels(K, np.arange(K), labels[ea], labels[eb])
+    out = labels.copy()
+    v = labels >= 0
+    out[v] = newlab[labels[v]]
+    return out, Kn, sel_eid
+
+
+def converged_test(t_done, E, params: Params):
+    """Stop rule of Algorithm 1: t = T, or relative energy change below dE_max.
+
+    Reading: the energy test compares two consecutive discontinuity-aware
+    iterations only (t_done >= 4).  The second alignment iteration re-solves an
+    already solved system, so a test there would end every run after the
+    alignment phase, against the iteration counts of 3 to 49 the paper reports.
+    A previous energy below 1e-300 counts as converged."""
+    if t_done >= params.T:
+        return True
+    if t_done >= 4:
+        e1, e0 = E[t_done], E[t_done - 1]
+        if e0 < 1e-300:
+            return True
+        return abs(e1 - e0) / e0 < params.dE_max
+    return False
+
+
+def scale_loop(geo: Geometry, labels, K, zt, params: Params, record=False):
+    """The relative-scale loop of Algorithm 1 (Sec. 3.4-3.5), from the filled
+    log-depth `zt` and partition `labels` (K components):
+      while not converged:
+        W_m^(t) = 1 if t <= 1 else W * W^out                   (Sec. 3.4)
+        s~ <- cg(A_m^T W A_m, A_m^T W b_m)                      (Eq. 14)
+        z~_c <- z~_c + s~_c 1                                   (Eqs. 7-8)
+        t <- t + 1
+        if can merge and t = 0 (mod freq_merging): merge       (Sec. 3.5)
+        E_t; converged <- |E_t - E_(t-1)| / E_(t-1) < dE_max or t = T
+    Reading: E_t is the energy of the system just solved, taken before any
+    merge of the same iteration.  Returns a dict (z~, labels, K, energies, ...)."""
+    params = Params.from_dict(dataclasses.asdict(params)) if isinstance(params, Params) else Params.from_dict(params)
+    zt = np.where(geo.valid, np.nan_to_num(zt), 0.0)
+    labels = labels.copy()
+    E = {0: np.finfo(np.float64).eps}
+    Ks = [K]
+    t = 0
+    merges = []
+    steps = []
+    e = inter_edges(geo, labels)
+    qcc, nq = quotient_components(K, labels, geo, e)
+    while True:
+        A, rhs, w, e = scale_system(geo, labels, K, zt, t, params, e)
+        s, it = solve_scales(A, rhs, w, K, qcc, nq)
+        zt = zt + np.where(geo.valid, s[np.maximum(labels, 0)], 0.0)
+        E_t = energy(A, rhs, w, s)
+        t += 1
+        E[t] = E_t
+        if record:
+            steps.append(dict(t=t, K=K, n_inter=len(e), cg_iters=it, s=s.copy(), E=E_t,
+                              z=zt.copy(), labels=labels.copy()))
+        if params.can_merge and t % params.freq_merging == 0:
+            chi = np.abs(residual(geo, zt, e)).astype(np.float32)
+            labels, K, sel = merge_labels(labels, K, geo, e, chi)
+            merges.append(dict(t=t, K=K, selected=sel, labels=labels.copy()))
+            e = inter_edges(geo, labels)
+            qcc, nq = quotient_components(K, labels, geo, e)
+        Ks.append(K)
+        if converged_test(t, E, params):
+            break
+    return dict(z=np.where(geo.valid, zt, np.nan), labels=labels, K=K, Ks=Ks,
+                energies=[E[i] for i in range(1, t + 1)], iters=t, merges=merges, steps=steps)
+
+
+def integrate(normals, mask, cam, params, record=False):
+    """Algorithm 1 end to end: seeding (Sec. 3.3), fill (Eqs. 9-10), then the
+    relative-scale loop with optional merging (Sec. 3.4-3.5).  Returns a dict
+    with z (log-depth, or depth for the orthographic reading, [H, W], NaN
+    invalid), depth (exp(z) for perspective), labels0/K0 after seeding, the
+    final labels/K, the energies E_1..E_t and the iteration count."""
+    if isinstance(cam, dict):
+        cam = Camera.from_dict(cam)
+    if isinstance(params, dict):
+        params = Params.from_dict(params)
+    mask = np.asarray(mask).astype(np.uint8)
+    H, W = mask.shape
+    geo = geometry(normals, mask, cam)
+    labels, K = seed_components(normals, mask, params.theta_c_deg)
+    zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls)
+    r = scale_loop(geo, labels, K, zt, params, record)
+    out = r["z"].reshape(H, W)
+    depth = np.exp(out) if cam.camera == PERSP else out
+    r.update(z=out, depth=depth, z_fill=zt.reshape(H, W), labels0=labels.reshape(H, W), K0=K,
+             labels=r["labels"].reshape(H, W), fill_iters=fill_iters)
+    return r
+
+
+# ---------------------------------------------------------------------------
+# evaluation helpers (alignment of Sec. 4; readings documented in the design doc)
+# ---------------------------------------------------------------------------
+
+def islands(mask):
+    """Connected components of the valid-pixel graph G_0 (4-connectivity)."""
+    H, W = mask.shape
+    a, b, _ = edge_list(mask)
+    vidx = np.nonzero(mask.reshape(-1))[0]
+    lab, n = canonical_labels(H * W, vidx, a, b)
+    out = np.full(H * W, -1, np.int64)
+    out[vidx] = lab
+    return out.reshape(H, W), n
+
+
+def aligned_rel_rmse(z, z_ref, mask, camera):
+    """Relative depth RMSE of `z` against `z_ref` after the alignment the
+    comparison needs, island by island (each island of the mask is
+    reconstructed up to its own scale/offset):
+      perspective: scale s* = <z, z_ref>/<z, z> per island, error / RMS(z_ref);
+      orthographic: offset o* = mean(z_ref - z) per island, error / (max - min)(z_ref)."""
+    isl, n = islands(mask)
+    m = isl >= 0
+    z = np.asarray(z, np.float64)
+    zr = np.asarray(z_ref, np.float64)
+    al = np.zeros_like(zr)
+    for i in range(n):
+        s = isl == i
+        if camera == PERSP:
+            den = np.sum(z[s] * z[s])
+            al[s] = z[s] * (np.sum(z[s] * zr[s]) / den if den > 0 else 1.0)
+        else:
+            al[s] = z[s] + np.mean(zr[s] - z[s])
+    err = np.sqrt(np.mean((al[m] - zr[m]) ** 2))
+    if camera == PERSP:
+        return float(err / np.sqrt(np.mean(zr[m] ** 2)))
+    return float(err / max(np.ptp(zr[m]), 1e-300))
