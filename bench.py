@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Throughput of continuous-component normal integration on one GB300.
+
+One step = one pass of the whole hot path (seeding, fill, relative-scale loop
+with merging, output) over one synthetic normal map through ni_integrate.
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(the reference arm of this build) on a bounded sample of the same workload.
+
+Multi-GPU: replicas only (each rank integrates its own copy of the map; the
+method has no exchange step on one map in this build), value = all ranks'
+valid pixels / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("valid Mpixel/s integrated at ≤1e-3 rel depth RMSE vs FP64 oracle; "
+          "stencil GB/s vs HBM peak")
+UNIT = "Mpixel/s"
+# algorithmic bytes of one batched-PCG iteration per active pixel: read p, x, r
+# (4 B each), the right/down weights (8 B), the inverse diagonal (4 B) and the
+# component label (4 B); write p, x, r (4 B each)
+PCG_BYTES_PER_PX_ITER = 40
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3")
+    ap.add_argument("--variant", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        rows = [r for r in self.rows if len(r) >= 10]
+        if self.uuid:
+            mine = [r for r in rows if self.uuid in r[1]]
+            rows = mine or rows
+        if not rows:
+            return None
+        idx0 = rows[0][0]
+        rows = [r for r in rows if r[0] == idx0]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        mx = [num(r[3]) for r in rows if num(r[3]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        load = [v for v in sm if mx and v >= 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_per_px_iter():
+    """DRAM bytes per active pixel-iteration of the batched PCG kernel from the
+    committed ncu summary, if it was taken on the current kernel source."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "pcg_batched_traffic.json")
+    src = os.path.join(ROOT, "paper_2510_11508_gb300", "csrc", "ni_fill.cu")
+    try:
+        d = json.load(open(p))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("source_sha256") != h:
+            return None
+        return float(d["dram_bytes_per_px_iter"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2510_11508_gb300 import ni
+    from synth import make_workload
+
+    w = make_workload(args.config)
+    H, W = w.mask.shape
+    params = dict(w.params)
+    cfg = ni.config_for(H, W, w.camera, params, batched=1 if args.variant == "batched" else 0,
+                        precision=args.precision)
+    it = ni.Integrator(cfg)
+    n = torch.from_numpy(w.normals).cuda()
+    m = torch.from_numpy(w.mask).cuda()
+    n_valid = int(w.mask.sum())
+
+    # accuracy against the FP64 oracle (rank 0), which is also the CPU baseline
+    check = None
+    cpu = None
+    depth, labels, st = it.integrate(n, m)
+    torch.cuda.synchronize()
+    if rank == 0 and not args.no_check:
+        import oracle as O
+        t0 = time.perf_counter()
+        ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(params))
+        dt = time.perf_counter() - t0
+        d = depth.cpu().numpy()
+        err = O.aligned_rel_rmse(np.where(w.mask > 0, d, np.nan), ref["depth"], w.mask, w.camera["camera"])
+        lab_ok = bool(np.array_equal(labels.cpu().numpy(), ref["labels"]))
+        check = {"rel_rmse_vs_oracle": err, "labels_bit_exact": lab_ok, "K0": st["K0"],
+                 "K_final": st["K_final"], "oracle_K_final": ref["K"], "iters": st["scale_iters"],
+                 "oracle_iters": ref["iters"], "tolerance": 1e-4 if args.precision == 0 else 1e-3}
+        cpu = {"value": n_valid / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full {w.name} workload ({n_valid} valid px), one run, {dt:.1f} s"}
+
+    for _ in range(args.warmup):
+        it.integrate(n, m)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fill_ms, px_iters, launches = 0.0, 0, 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        depth, labels, st = it.integrate(n, m)
+        fill_ms += st["ms_fill_solve"]
+        px_iters += st["fill_px_iters"]
+        launches += st["kernel_launches"] + 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_valid * args.steps * world / (ms / 1e3) / 1e6
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    nh = torch.from_numpy(w.normals).pin_memory()
+    mh = torch.from_numpy(w.mask).pin_memory()
+    out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    it.integrate_host(nh, mh, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        it.integrate_host(nh, mh, out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": n_valid * args.steps * world / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(nh.numel() * 4 + mh.numel()),
+           "d2h_bytes_per_step": int(out.numel() * 4)}
+
+    peak, peak_src = peaks()
+    per_launch_ms = fill_ms / args.steps
+    per_launch_bytes = PCG_BYTES_PER_PX_ITER * px_iters / args.steps
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
+    tpi = traffic_per_px_iter()
+    roof = {"kernel": "k_pcg_batched" if args.variant == "batched" else "plain PCG (k_cg_*)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
+            "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": (tpi * px_iters / args.steps) if tpi is not None else None,
+            "algorithmic_bytes_per_launch": per_launch_bytes,
+            "bytes_per_px_iter": PCG_BYTES_PER_PX_ITER,
+            "px_iters_per_launch": px_iters / args.steps, "ms_per_launch": per_launch_ms}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "description": w.description, "H": H, "W": W,
+                       "n_valid": n_valid, "variant": args.variant,
+                       "reductions": "fp64" if args.precision == 0 else "fp32 tree + fp64 across CTAs",
+                       "theta_c_deg": params["theta_c_deg"], "T": params["T"],
+                       "can_merge": params["can_merge"], "freq_merging": params["freq_merging"],
+                       "l2": "flushed between steps (256 MiB write inside the timed region)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks, "check": check,
+            "stages_ms": {k: st[k] for k in ("ms_seed", "ms_fill", "ms_scale", "ms_output", "ms_total")},
+            "fill_iters": st["fill_iters"], "scale_iters": st["scale_iters"],
+            "K0": st["K0"], "K_final": st["K_final"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    it.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    import numpy as np
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from synth import make_workload
+
+    w = make_workload(args.config)
+    crop = 512
+    nrm = np.ascontiguousarray(w.normals[:crop, :crop])
+    msk = np.ascontiguousarray(w.mask[:crop, :crop])
+    n_valid = int(msk.sum())
+    p = O.Params.from_dict(w.params)
+    for _ in range(args.warmup):
+        O.integrate(nrm, msk, w.camera, p)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.integrate(nrm, msk, w.camera, p)
+    dt = time.perf_counter() - t0
+    value = n_valid * args.steps / dt / 1e6
+    sample = f"top-left {crop}x{crop} crop of {w.name} ({n_valid} valid px) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "sample": sample, "variant": "fp64 CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,62 @@
+"""Algorithm 1 end to end through ni_integrate against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import make_workload
+
+from gpu_util import dev, integrator, rel_depth_error
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(name, **over):
+    w = make_workload(name)
+    p = dict(w.params, **over)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, p)
+    depth, labels, st = it.integrate(n, m)
+    ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(p))
+    return w, depth.cpu().numpy(), labels.cpu().numpy(), st, ref
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3_small"])
+def test_integrate_matches_oracle(name):
+    w, depth, labels, st, ref = _run(name)
+    zg = np.log(depth) if w.camera["camera"] == 1 else depth
+    zr = np.nan_to_num(ref["z"])
+    err = rel_depth_error(np.nan_to_num(zg), zr, w.mask, w.camera["camera"])
+    print(name, "stats", {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "merges")},
+          "oracle K0", ref["K0"], "K", ref["K"], "iters", ref["iters"], "err", err)
+    assert st["K0"] == ref["K0"]
+    assert np.isnan(depth[w.mask == 0]).all()
+    if st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]:
+        np.testing.assert_array_equal(labels, ref["labels"])
+        assert err <= 1e-4
+    else:
+        pytest.fail(f"partition or iteration count differs: {st} vs oracle K={ref['K']} iters={ref['iters']}")
+
+
+def test_integrate_host_equals_device():
+    w = make_workload("c2")
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params)
+    d_dev, _, _ = it.integrate(n, m)
+    nh = torch.from_numpy(w.normals).pin_memory()
+    mh = torch.from_numpy(w.mask).pin_memory()
+    out = torch.empty((H, W), dtype=torch.float32).pin_memory()
+    it.integrate_host(nh, mh, out)
+    a, b = d_dev.cpu().numpy(), out.numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert np.nanmax(np.abs(a - b) / np.abs(b)) < 1e-5
+
+
+def test_full_size_c3():
+    w, depth, labels, st, ref = _run("c3")
+    zg = np.log(depth)
+    err = rel_depth_error(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, 1)
+    print("c3", st, "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
+    assert st["K0"] == ref["K0"]

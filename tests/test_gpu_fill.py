@@ -1,0 +1,73 @@
+"""Component fill (Sec. 3.3, Eqs. 9-10): the GPU's per-component log-depth
+against the oracle's minimum-norm least-squares solution.
+
+Tolerance: the build's accuracy bound is a relative depth RMSE of 1e-4 for the
+FP64-reduction path and 1e-3 for the reduced-precision path; an error dz in
+log-depth is a relative depth error of dz, so the same numbers bound the RMS of
+the log-depth difference (orthographic: relative to the depth range)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import generators as G, make_workload
+
+from gpu_util import dev, integrator, island_rms
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-4, 1: 1e-3}
+
+
+def _fill_pair(normals, mask, camera, params, **over):
+    H, W = mask.shape
+    n, m = dev(normals, mask)
+    it = integrator(H, W, camera, params, **over)
+    lab, K = it.seed_components(n, m)
+    z = it.solve_components().cpu().numpy()
+    cam = O.Camera.from_dict(camera)
+    geo = O.geometry(normals, mask, cam)
+    ref_lab, Kr = O.seed_components(normals, mask, params["theta_c_deg"])
+    assert K == Kr
+    zr, _ = O.fill_components(geo, ref_lab, Kr, params.get("k", 2.0), params.get("n_fill_irls", 1))
+    zr = np.nan_to_num(zr).reshape(mask.shape)
+    return z, zr, K
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3_small"])
+@pytest.mark.parametrize("batched", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fill_matches_oracle(name, batched, precision):
+    w = make_workload(name)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=batched, precision=precision)
+    m = w.mask > 0
+    # per-component zero mean on both sides: compare directly
+    d = (z - zr)[m]
+    scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[m]))
+    rms = float(np.sqrt(np.mean(d * d))) / scale
+    print(f"{name} batched={batched} prec={precision} K={K} fill rms={rms:.3e} max={np.abs(d).max():.3e}")
+    assert rms <= TOL[precision]
+
+
+@pytest.mark.parametrize("batched", [0, 1])
+def test_fill_exact_plane(batched):
+    nrm, mask, z, cam = G.plane_map(40, 53, G.PERSP, normal=(0.3, -0.2, -1.0), d=30.0, dtype=np.float32)
+    zf, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 5.0}, batched=batched)
+    assert K == 1
+    rms, mx = island_rms(zf, np.log(z), mask)
+    assert rms < 2e-6, rms
+
+
+def test_fill_random_ragged_with_holes():
+    nrm, mask, cam = G.random_normal_field(45, 77, n_dirs=2, jitter_deg=0.8, hole_frac=0.05, seed=3,
+                                           block=9)
+    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1)
+    d = (z - zr)[mask > 0]
+    assert np.sqrt(np.mean(d * d)) < 1e-4
+
+
+def test_fill_irls_sweeps():
+    w = make_workload("c3_small")
+    p = dict(w.params, n_fill_irls=2)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1)
+    d = (z - zr)[w.mask > 0]
+    assert np.sqrt(np.mean(d * d)) < 1e-4
