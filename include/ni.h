@@ -198,6 +198,31 @@ ni_status ni_get_logdepth(ni_handle* h, float* logdepth_out, ni_stream_t stream)
  * NI_ERR_INVALID_ARG if the file is missing or malformed. */
 ni_status ni_load_net(ni_handle* h, const char* path);
 
+/* Seeding without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory while they
+ * run -- for example a real-time pipeline that reserves all memory at start-up,
+ * a host framework whose allocator owns the device, or code where cudaMalloc
+ * would synchronise the device or fail under a fixed memory-pool limit.  It
+ * computes exactly what ni_seed_components computes (same kernels, same
+ * canonical labels) without a handle: the union-find parent array, the scan
+ * partials and the counters live in one file-scope device array of
+ * 16 MiB + 16 KiB that every GPU which loads this library keeps until the
+ * process exits.
+ *   normals, mask: device, as for ni_seed_components (normals 16-byte aligned);
+ *   cam, theta_c_deg: as in ni_config (theta_c_deg < 0 = None); normals are
+ *     not validated;
+ *   labels_out: device int32[H][W]; K_out_device: device int32[1] receiving K.
+ * Limit: H * W <= 4,194,304 (2^22) pixels; larger maps (and bad sizes or
+ * pointers) return NI_ERR_INVALID_ARG without touching the GPU.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, so calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Asynchronous on
+ * `stream`; calls no cudaMalloc, cudaFree or allocating library routine. */
+ni_status ni_seed_components_noalloc(const float* normals, const uint8_t* mask, int H, int W,
+                                     const ni_camera* cam, double theta_c_deg, int32_t* labels_out,
+                                     int32_t* K_out_device, ni_stream_t stream);
+
 /* Message of the last error on this handle ("" if none); never NULL. */
 const char* ni_last_error(const ni_handle* h);
 

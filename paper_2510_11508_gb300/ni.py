@@ -23,7 +23,7 @@ STATUS = {0: "NI_OK", 1: "NI_ERR_INVALID_ARG", 2: "NI_ERR_CUDA", 3: "NI_ERR_OOM"
 EXPORTS = ["ni_config_default", "ni_create", "ni_destroy", "ni_seed_components",
            "ni_solve_components", "ni_solve_scales", "ni_merge", "ni_merge_residuals",
            "ni_integrate", "ni_integrate_host", "ni_get_logdepth", "ni_load_net", "ni_last_error",
-           "ni_status_string"]
+           "ni_status_string", "ni_seed_components_noalloc"]
 
 
 class Camera(C.Structure):
@@ -88,6 +88,8 @@ def load(build_if_missing: bool = False):
     L.ni_integrate.argtypes = [vp, vp, vp, vp, vp, C.POINTER(Stats), vp]
     L.ni_integrate_host.argtypes = [vp, vp, vp, vp, C.POINTER(Stats), vp]
     L.ni_get_logdepth.argtypes = [vp, vp, vp]
+    L.ni_seed_components_noalloc.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(Camera), C.c_double,
+                                             vp, vp, vp]
     L.ni_load_net.argtypes = [vp, C.c_char_p]
     L.ni_last_error.argtypes = [vp]
     L.ni_last_error.restype = C.c_char_p
