@@ -176,18 +176,30 @@ extern "C" ni_status ni_create(const ni_config* cfg, ni_handle** out) {
   h->cos_theta = cfg->theta_c_deg < 0 ? 2.0 : cos(cfg->theta_c_deg * (M_PI / 180.0));
   cudaError_t e = cudaGetDevice(&h->dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->dev);
-  const size_t N = (size_t)h->N;
-  if (e == cudaSuccess) e = dalloc(&h->labels, N);
+  h->ntx = (h->W + NI_TILE_W - 1) / NI_TILE_W;
+  h->ntiles = h->ntx * ((h->H + NI_TILE_H - 1) / NI_TILE_H);
+  h->Npad = (h->N + NI_TILE_PX - 1) / NI_TILE_PX * NI_TILE_PX;
+  const size_t N = (size_t)h->N, NP = (size_t)h->Npad;
+  if (e == cudaSuccess) e = dalloc(&h->labels, NP);
   if (e == cudaSuccess) e = dalloc(&h->parent, N);
   if (e == cudaSuccess) e = dalloc(&h->omega, N);
   if (e == cudaSuccess) e = dalloc(&h->ntau, N);
-  if (e == cudaSuccess) e = dalloc(&h->wfill, N);
-  if (e == cudaSuccess) e = dalloc(&h->invd, N);
-  if (e == cudaSuccess) e = dalloc(&h->x, N);
-  if (e == cudaSuccess) e = dalloc(&h->r, N);
-  if (e == cudaSuccess) e = dalloc(&h->p, N);
-  if (e == cudaSuccess) e = dalloc(&h->q, N);
-  if (e == cudaSuccess) e = dalloc(&h->b, N);
+  if (e == cudaSuccess) e = dalloc(&h->wr, NP);
+  if (e == cudaSuccess) e = dalloc(&h->wd, NP);
+  if (e == cudaSuccess) e = dalloc(&h->invd, NP);
+  if (e == cudaSuccess) e = dalloc(&h->x, NP);
+  if (e == cudaSuccess) e = dalloc(&h->r, NP);
+  if (e == cudaSuccess) e = dalloc(&h->p, NP);
+  if (e == cudaSuccess) e = dalloc(&h->p2, NP);
+  if (e == cudaSuccess) e = dalloc(&h->q, NP);
+  if (e == cudaSuccess) e = dalloc(&h->b, NP);
+  if (e == cudaSuccess) e = dalloc(&h->tile_lab, (size_t)h->ntiles);
+  if (e == cudaSuccess) e = dalloc(&h->tiles, 2 * (size_t)h->ntiles);
+  // padding pixels beyond N: label -1, weights and vectors 0 (never written later)
+  if (e == cudaSuccess) e = cudaMemset(h->labels, 0xff, NP * sizeof(int32_t));
+  float* zero_planes[] = {h->wr, h->wd, h->invd, h->x, h->r, h->p, h->p2, h->q, h->b};
+  for (float* zp : zero_planes)
+    if (e == cudaSuccess) e = cudaMemset(zp, 0, NP * sizeof(float));
   if (e == cudaSuccess) e = dalloc(&h->blk, NI_SCAN_BLOCKS + 1);
   if (e == cudaSuccess) e = dalloc(&h->d_count, 16);
   if (e == cudaSuccess) e = dalloc(&h->radix_hist, 256 * NI_SORT_BLOCKS);
@@ -207,7 +219,8 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   destroy_graph(h);
   release_components(h);
   release_edges(h);
-  dfree(h->labels); dfree(h->parent); dfree(h->omega); dfree(h->ntau); dfree(h->wfill);
+  dfree(h->labels); dfree(h->parent); dfree(h->omega); dfree(h->ntau); dfree(h->wr); dfree(h->wd);
+  dfree(h->tile_lab); dfree(h->tiles);
   dfree(h->invd); dfree(h->x); dfree(h->r); dfree(h->p); dfree(h->p2); dfree(h->q); dfree(h->b);
   dfree(h->blk); dfree(h->d_count); dfree(h->radix_hist); dfree(h->st);
   dfree(h->in_normals); dfree(h->in_mask); dfree(h->out_depth);

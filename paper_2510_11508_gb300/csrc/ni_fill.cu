@@ -15,14 +15,20 @@
 //   which is the edge's entry in A_c^T W_c A_c (rows of both directions);
 //   right-hand side b_a = sum_b w_ab omega~_{b->a} (= A_c^T W_c b_c);
 //   Jacobi diagonal d_a = sum_b w_ab.
+// Weights are two planes, wr[a] (edge a - a+1) and wd[a] (edge a - a+W); the
+// left and upper weights of a are wr[a-1] and wd[a-W].  Because wr is 0 in the
+// last column, raster-linear indexing needs no row tests: wr[a-1] is 0 when a
+// starts a row.
 //
 // Solve: Jacobi-preconditioned CG on the block-diagonal weighted Laplacian,
 //   matrix-free 5-point stencil in float32, reductions in float64 (or float32
 //   warp/CTA trees, precision = 1):
 //   plain   (batched = 0): one global CG; three kernels per iteration,
 //           iteration chunks replayed from a CUDA graph;
-//   batched (batched = 1): one cooperative persistent launch with a step
-//           length, direction update and convergence mask per component.
+//   batched (batched = 1): k_pcg_tiles, one cooperative persistent launch with
+//           a step length, direction update and convergence mask per component,
+//           working on a list of 1024-pixel tiles that still hold an active
+//           component.
 // Both start from x0 (0 or the warm start), project the right-hand side and the
 // result to zero mean per component (the gauge CG from 0 reaches).
 #include <algorithm>
@@ -42,7 +48,7 @@ static int grid_px(ni_handle* h, long long n, int threads = 256) {
 __global__ void k_edge_setup(const float4* __restrict__ nrm, const uint8_t* __restrict__ mask,
                              const int* __restrict__ labels, int H, int W, int persp, float fx,
                              float fy, float cx, float cy, float2* __restrict__ omega,
-                             float* __restrict__ ntau, float2* __restrict__ wfill) {
+                             float* __restrict__ ntau, float* __restrict__ wr, float* __restrict__ wd) {
   const int N = H * W;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     float2 om = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
@@ -88,24 +94,27 @@ __global__ void k_edge_setup(const float4* __restrict__ nrm, const uint8_t* __re
     }
     omega[a] = om;
     ntau[a] = A;
-    wfill[a] = w;
+    wr[a] = w.x;
+    wd[a] = w.y;
   }
 }
 
 // Jacobi inverse diagonal and right-hand side b_a = sum_b w_ab omega~_{b->a}.
-__global__ void k_diag_rhs(const float2* __restrict__ wfill, const float2* __restrict__ omega, int H,
-                           int W, float* __restrict__ invd, float* __restrict__ rhs) {
+__global__ void k_diag_rhs(const float* __restrict__ wr, const float* __restrict__ wd,
+                           const float2* __restrict__ omega, int H, int W, float* __restrict__ invd,
+                           float* __restrict__ rhs) {
   const int N = H * W;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
-    const int u = a % W, v = a / W;
-    const float2 w = wfill[a], om = omega[a];
+    const int v = a / W;
+    const float2 om = omega[a];
+    const float wra = wr[a], wda = wd[a];
     float wl = 0.f, wu = 0.f, ol = 0.f, ou = 0.f;
-    if (u > 0) { wl = wfill[a - 1].x; ol = omega[a - 1].x; }
-    if (v > 0) { wu = wfill[a - W].y; ou = omega[a - W].y; }
-    const float d = w.x + w.y + wl + wu;
+    if (a > 0) { wl = wr[a - 1]; ol = omega[a - 1].x; }
+    if (v > 0) { wu = wd[a - W]; ou = omega[a - W].y; }
+    const float d = wra + wda + wl + wu;
     invd[a] = d > 0.f ? 1.0f / d : 0.f;
     // omega~_{l->a} = -omega~_{a->l} (antisymmetry of Eq. 3)
-    rhs[a] = w.x * om.x + w.y * om.y - wl * ol - wu * ou;
+    rhs[a] = wra * om.x + wda * om.y - wl * ol - wu * ou;
   }
 }
 
@@ -120,31 +129,29 @@ __device__ __forceinline__ float bini_w(float gam, float za, float zb, float zo,
 
 __global__ void k_fill_reweight(const float* __restrict__ ntau, const int* __restrict__ labels,
                                 const float* __restrict__ x, int H, int W, int persp, float fx,
-                                float fy, float k, float2* __restrict__ wfill) {
+                                float fy, float k, float* __restrict__ wr, float* __restrict__ wd) {
   const int N = H * W;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
-    float2 w = wfill[a];
     const int la = labels[a];
     const int u = a % W, v = a / W;
-    if (la >= 0 && w.x > 0.f) {
+    if (la >= 0 && wr[a] > 0.f) {
       const int b = a + 1;
       float f = persp ? fx : 1.f;
       float gba = f * ntau[a], gab = f * ntau[b];
       bool ho_a = (u > 0) && labels[a - 1] == la;
       bool ho_b = (u + 2 < W) && labels[b + 1] == la;
-      w.x = bini_w(gba, x[a], x[b], ho_a ? x[a - 1] : 0.f, ho_a, k) +
-            bini_w(gab, x[b], x[a], ho_b ? x[b + 1] : 0.f, ho_b, k);
+      wr[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - 1] : 0.f, ho_a, k) +
+              bini_w(gab, x[b], x[a], ho_b ? x[b + 1] : 0.f, ho_b, k);
     }
-    if (la >= 0 && w.y > 0.f) {
+    if (la >= 0 && wd[a] > 0.f) {
       const int b = a + W;
       float f = persp ? fy : 1.f;
       float gba = f * ntau[a], gab = f * ntau[b];
       bool ho_a = (v > 0) && labels[a - W] == la;
       bool ho_b = (v + 2 < H) && labels[b + W] == la;
-      w.y = bini_w(gba, x[a], x[b], ho_a ? x[a - W] : 0.f, ho_a, k) +
-            bini_w(gab, x[b], x[a], ho_b ? x[b + W] : 0.f, ho_b, k);
+      wd[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W] : 0.f, ho_a, k) +
+              bini_w(gab, x[b], x[a], ho_b ? x[b + W] : 0.f, ho_b, k);
     }
-    wfill[a] = w;
   }
 }
 
@@ -172,21 +179,60 @@ __global__ void k_comp_sub_mean(const int* __restrict__ labels, int N, const dou
   }
 }
 
+// Tiles are 32 x 32 pixel blocks (the last row / column of tiles may be cut by
+// the image border).  Thread t of a 256-thread CTA owns the 4 pixels of tile row
+// t / 8 starting at tile column 4 (t % 8).
+struct G4 {
+  int a;     // raster index of the first pixel
+  int row, col;
+  int nval;  // pixels of the group inside the image (0..4)
+};
+
+__device__ __forceinline__ G4 group_of(int t, int ntx, int H, int W) {
+  G4 g;
+  g.row = (t / ntx) * NI_TILE_H + (threadIdx.x >> 3);
+  g.col = (t % ntx) * NI_TILE_W + ((threadIdx.x & 7) << 2);
+  g.nval = g.row < H ? max(0, min(4, W - g.col)) : 0;
+  g.a = g.row * W + g.col;
+  return g;
+}
+
+// Label shared by every valid pixel of a tile (-1 when several labels meet,
+// -2 when the tile holds no valid pixel).
+__global__ void k_tile_labels(const int* __restrict__ labels, int ntiles, int ntx, int H, int W,
+                              int* __restrict__ tile_lab) {
+  __shared__ int smin, smax;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    if (threadIdx.x == 0) { smin = 0x7fffffff; smax = -1; }
+    __syncthreads();
+    const G4 g = group_of(t, ntx, H, W);
+    int mn = 0x7fffffff, mx = -1;
+    for (int j = 0; j < g.nval; ++j) {
+      const int l = labels[g.a + j];
+      if (l >= 0) { mn = min(mn, l); mx = max(mx, l); }
+    }
+    atomicMin(&smin, mn);
+    atomicMax(&smax, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) tile_lab[t] = smax < 0 ? -2 : (smin == smax ? smin : -1);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
-// stencil helpers
+// plain Jacobi-PCG (global step lengths)
 // ---------------------------------------------------------------------------
 struct Stencil {
   float wr, wd, wl, wu;
 };
 
-__device__ __forceinline__ Stencil load_stencil(const float2* __restrict__ wfill, int a, int u, int v,
-                                                int W) {
-  const float2 w = wfill[a];
+__device__ __forceinline__ Stencil load_stencil(const float* __restrict__ wr, const float* __restrict__ wd,
+                                                int a, int W) {
   Stencil s;
-  s.wr = w.x;
-  s.wd = w.y;
-  s.wl = (u > 0) ? wfill[a - 1].x : 0.f;
-  s.wu = (v > 0) ? wfill[a - W].y : 0.f;
+  s.wr = wr[a];
+  s.wd = wd[a];
+  s.wl = (a > 0) ? wr[a - 1] : 0.f;
+  s.wu = (a >= W) ? wd[a - W] : 0.f;
   return s;
 }
 
@@ -203,9 +249,6 @@ __device__ __forceinline__ float apply_stencil(const Stencil& s, const float* __
   return acc;
 }
 
-// ---------------------------------------------------------------------------
-// plain Jacobi-PCG (global step lengths)
-// ---------------------------------------------------------------------------
 template <typename Acc>
 __device__ __forceinline__ void block_atomic_add(double* dst, Acc v, double* sh) {
   double t = block_sum_d((double)v, sh);
@@ -213,15 +256,15 @@ __device__ __forceinline__ void block_atomic_add(double* dst, Acc v, double* sh)
 }
 
 template <typename Acc>
-__global__ void k_cg_init(const float2* __restrict__ wfill, const float* __restrict__ invd,
-                          const float* __restrict__ rhs, const float* __restrict__ x,
-                          float* __restrict__ r, float* __restrict__ p, int H, int W, DevState* st) {
+__global__ void k_cg_init(const float* __restrict__ wr, const float* __restrict__ wd,
+                          const float* __restrict__ invd, const float* __restrict__ rhs,
+                          const float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, int H,
+                          int W, DevState* st) {
   __shared__ double sh[33];
   const int N = H * W;
   Acc rz = 0, rr = 0, bb = 0;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
-    const int u = a % W, v = a / W;
-    Stencil s = load_stencil(wfill, a, u, v, W);
+    Stencil s = load_stencil(wr, wd, a, W);
     float ra = rhs[a] - apply_stencil(s, x, a, W, x[a]);
     if (invd[a] == 0.f) ra = 0.f;
     float z = ra * invd[a];
@@ -245,15 +288,14 @@ __global__ void k_cg_init_done(DevState* st, double tol2) {
 }
 
 template <typename Acc>
-__global__ void k_cg_spmv(const float2* __restrict__ wfill, const float* __restrict__ p,
-                          float* __restrict__ q, int H, int W, DevState* st) {
+__global__ void k_cg_spmv(const float* __restrict__ wr, const float* __restrict__ wd,
+                          const float* __restrict__ p, float* __restrict__ q, int H, int W, DevState* st) {
   __shared__ double sh[33];
   if (*(volatile int*)&st->cg_done) return;
   const int N = H * W;
   Acc pap = 0;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
-    const int u = a % W, v = a / W;
-    Stencil s = load_stencil(wfill, a, u, v, W);
+    Stencil s = load_stencil(wr, wd, a, W);
     const float pa = p[a];
     q[a] = apply_stencil(s, p, a, W, pa);
     // p^T A p as the sum over edges of w (p_a - p_b)^2 (no cancellation)
@@ -317,201 +359,568 @@ __global__ void k_cg_dir(const float* __restrict__ invd, const float* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// batched persistent Jacobi-PCG: per-component step lengths and masks
+// batched persistent Jacobi-PCG over active tiles
 // ---------------------------------------------------------------------------
-// Per-component slots in cacc (each Kcap doubles):
-//   0,1 rz (iteration parity)   2,3 p^T A p   4,5 rz_new   6,7 r^T r   8 b^T b
-//   9 sum x   10 count
-// cflag: [0, Kcap) active flag parity 0, [Kcap, 2 Kcap) parity 1, [2 Kcap, 3 Kcap) iterations
+// Per-component state (doubles, Kc each): 0,1 rz of iteration parity; 2,3 p^T A p;
+// 4,5 rz_new; 6,7 r^T r; 8 b^T b; 9 sum x; 10 count.
+// Per-component ints: [0, 2 Kc) active flag per parity; [2 Kc, 3 Kc) iterations.
+// Iteration k (parity P = k & 1, Q = P ^ 1), on the tiles of list Q (active at k-1):
+//  phase 1: deferred update x += alpha_{k-1} p_{k-1}; for components still active
+//           p_k = D^-1 r + beta_k p_{k-1} (own pixels and stencil neighbours; a
+//           neighbour joined by a nonzero weight is in the same component, so it
+//           shares beta), q = A p_k, p_k^T A p_k; tiles with an active pixel go to
+//           list P.  One thread per component moves rz_new_{k-1} into rz_k, sets
+//           the flag of iteration k and clears the accumulators of parity P.
+//  phase 2: alpha_k = rz_k / p^T A p; r -= alpha_k q; r^T D^-1 r and r^T r.
+// A bounded grid barrier separates the phases.  Per-component sums: a tile whose
+// valid pixels share one label is reduced by the CTA (one atomic per value);
+// otherwise runs of equal labels across a warp are summed, the run totals are
+// gathered per label in a shared-memory table, and the table is flushed with
+// one atomic per label and value.
 struct PcgArgs {
-  const float2* wfill;
+  const float* wr;
+  const float* wd;
   const float* invd;
   const float* rhs;
   const int* labels;
+  const int* tile_lab;
   float* x;
   float* r;
-  float* p;
+  float* pb0;
+  float* pb1;
   float* q;
-  double* cacc;
-  int* cflag;
+  double* cs;
+  int* ci;
+  int* tiles;      // [2][ntiles]
+  int* ntl;        // [2] list lengths
   DevState* st;
-  int* active_cnt;   // [2]
-  int H, W, K, Kcap;
-  int maxit;
+  int N, H, W, K, Kc, ntiles, ntx, maxit;
   double tol2;
 };
 
-template <bool FP64>
-__device__ __forceinline__ void seg_add_one(double* acc, int key, float a) {
-  if (FP64) {
-    double v[1] = {(double)a};
-    seg_add_d<1>(acc, 1, key, v);
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float f4get(const float4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4set(float4& v, int j, float s) {
+  if (j == 0) v.x = s; else if (j == 1) v.y = s; else if (j == 2) v.z = s; else v.w = s;
+}
+
+// the 4 values of a group at raster index a (nval of them inside the image)
+template <bool ALIGNED>
+__device__ __forceinline__ float4 ldg(const float* p, int a, int nval) {
+  if (ALIGNED && nval == 4) return ld4(p + a);
+  return make_float4(nval > 0 ? p[a] : 0.f, nval > 1 ? p[a + 1] : 0.f, nval > 2 ? p[a + 2] : 0.f,
+                     nval > 3 ? p[a + 3] : 0.f);
+}
+template <bool ALIGNED>
+__device__ __forceinline__ void stg(float* p, int a, int nval, float4 v) {
+  if (ALIGNED && nval == 4) { st4(p + a, v); return; }
+  if (nval > 0) p[a] = v.x;
+  if (nval > 1) p[a + 1] = v.y;
+  if (nval > 2) p[a + 2] = v.z;
+  if (nval > 3) p[a + 3] = v.w;
+}
+template <bool ALIGNED>
+__device__ __forceinline__ void ldlab(const int* l, int a, int nval, int (&lab)[4]) {
+  if (ALIGNED && nval == 4) {
+    const int4 v = *reinterpret_cast<const int4*>(l + a);
+    lab[0] = v.x; lab[1] = v.y; lab[2] = v.z; lab[3] = v.w;
   } else {
-    float v[1] = {a};
-    seg_add_f<1>(acc, 1, key, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lab[j] = j < nval ? l[a + j] : -1;
   }
 }
 
-template <bool FP64>
-__global__ void __launch_bounds__(256) k_pcg_batched(PcgArgs A) {
-  const int H = A.H, W = A.W, N = H * W, K = A.K, Kc = A.Kcap;
-  double* rzb0 = A.cacc + 0 * (size_t)Kc;
-  double* pap0 = A.cacc + 2 * (size_t)Kc;
-  double* rzn0 = A.cacc + 4 * (size_t)Kc;
-  double* rr0 = A.cacc + 6 * (size_t)Kc;
-  double* bb = A.cacc + 8 * (size_t)Kc;
-  double* sx = A.cacc + 9 * (size_t)Kc;
-  int* iters = A.cflag + 2 * (size_t)Kc;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nthr = gridDim.x * blockDim.x;
-  const int nIter = (N + nthr - 1) / nthr;   // uniform trip count for the warp-level reductions
+#define TAB_SLOTS 64
+
+// Two-sum of float pairs (Knuth): hi + lo carries ~48 bits, the "compensated
+// FP32" reduction of the build (no FP64 instructions per pixel).
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (h2 - bp);
+  lo = lo + l2 + e;
+  hi = s;
+}
+
+template <bool COMP>
+__device__ __forceinline__ double warp_total(float v) {
+  if (COMP) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ff_add(hi, lo, __shfl_xor_sync(NI_FULL, hi, o), __shfl_xor_sync(NI_FULL, lo, o));
+    return (double)hi + (double)lo;
+  }
+  return (double)warp_sum_f(v);
+}
+
+// Add NV per-thread values into dst[v][label].  `key` is the label all of the
+// thread's contributing pixels share (-1: nothing to add; threads with pixels of
+// several labels add per pixel before calling, and pass -1).  ul >= 0: the whole
+// tile is one component.  Warp trees in float (float-float when COMP), the
+// per-warp totals in double.  All threads of the CTA call it.
+template <bool COMP, int NV>
+__device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV], double* const (&dst)[NV],
+                                           int* s_key, double* s_val, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (ul >= 0) {
+    double w[NV];
+#pragma unroll
+    for (int j = 0; j < NV; ++j) w[j] = warp_total<COMP>(v[j]);
+    if (lane == 0)
+#pragma unroll
+      for (int j = 0; j < NV; ++j) sh[wid * NV + j] = w[j];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+      double t = 0.0;
+      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += sh[ww * NV + threadIdx.x];
+      if (t != 0.0) atomicAdd(dst[threadIdx.x] + ul, t);
+    }
+    __syncthreads();
+    return;
+  }
+  // warp-segmented runs of equal keys
+  const int prev = __shfl_up_sync(NI_FULL, key, 1);
+  const int next = __shfl_down_sync(NI_FULL, key, 1);
+  const bool head = (lane == 0) || (prev != key);
+  const bool tail = (lane == 31) || (next != key);
+  const unsigned heads = __ballot_sync(NI_FULL, head);
+  const int my_head = 31 - __clz(heads & ((2u << lane) - 1u));
+  double acc[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    float hi = v[j], lo = 0.f;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float h2 = __shfl_up_sync(NI_FULL, hi, o);
+      const float l2 = COMP ? __shfl_up_sync(NI_FULL, lo, o) : 0.f;
+      if (lane - o >= my_head) {
+        if (COMP) ff_add(hi, lo, h2, l2);
+        else hi += h2;
+      }
+    }
+    acc[j] = (double)hi + (double)lo;
+  }
+  if (tail && key >= 0) {
+    int h = key & (TAB_SLOTS - 1), slot = -1;
+    for (int probe = 0; probe < TAB_SLOTS; ++probe) {
+      const int old = atomicCAS(&s_key[h], -1, key);
+      if (old == -1 || old == key) { slot = h; break; }
+      h = (h + 1) & (TAB_SLOTS - 1);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      if (acc[j] == 0.0) continue;
+      if (slot >= 0) atomicAdd(&s_val[slot * 3 + j], acc[j]);
+      else atomicAdd(dst[j] + key, acc[j]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < TAB_SLOTS) {
+    const int k = s_key[threadIdx.x];
+    if (k >= 0) {
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        const double t = s_val[threadIdx.x * 3 + j];
+        if (t != 0.0) atomicAdd(dst[j] + k, t);
+        s_val[threadIdx.x * 3 + j] = 0.0;
+      }
+      s_key[threadIdx.x] = -1;
+    }
+  }
+  __syncthreads();
+}
+
+// Per-tile cache of per-component scalars: each distinct label of the tile gets a
+// shared-memory slot; slot owners compute the label's scalars once (FP64), the
+// pixels read floats.  sl[j] = slot of pixel j, -1 for no label, -2 if the table
+// overflowed (the pixel then computes its own scalars).
+__device__ __forceinline__ void tile_slots(int ul, const int (&lab)[4], int (&sl)[4], int* s_lab) {
+  if (ul >= 0) {
+    if (threadIdx.x == 0) s_lab[0] = ul;
+    for (int i = 1 + threadIdx.x; i < TAB_SLOTS; i += blockDim.x) s_lab[i] = -1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sl[j] = lab[j] >= 0 ? 0 : -1;
+    __syncthreads();
+    return;
+  }
+  if (threadIdx.x < TAB_SLOTS) s_lab[threadIdx.x] = -1;
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    sl[j] = -1;
+    if (lab[j] < 0) continue;
+    if (j > 0 && lab[j] == lab[j - 1]) { sl[j] = sl[j - 1]; continue; }
+    int h = lab[j] & (TAB_SLOTS - 1);
+    sl[j] = -2;
+    for (int probe = 0; probe < TAB_SLOTS; ++probe) {
+      const int old = atomicCAS(&s_lab[h], -1, lab[j]);
+      if (old == -1 || old == lab[j]) { sl[j] = h; break; }
+      h = (h + 1) & (TAB_SLOTS - 1);
+    }
+  }
+  __syncthreads();
+}
+
+// key of a thread's contributing pixels (-1 none, -2 several labels)
+__device__ __forceinline__ int group_key(const int (&lab)[4], const bool (&on)[4]) {
+  int key = -1;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (on[j]) key = (key == -1 || key == lab[j]) ? lab[j] : -2;
+  return key;
+}
+
+template <int NV>
+__device__ __forceinline__ void group_values(int key, const int (&lab)[4], const bool (&on)[4],
+                                             const float (&pv)[NV][4], double* const (&dst)[NV],
+                                             float (&v)[NV]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.f;
+  if (key >= 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[i] += on[j] ? pv[i][j] : 0.f;
+  } else if (key == -2) {   // pixels of several labels: add them one by one
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (on[j])
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+          if (pv[i][j] != 0.f) atomicAdd(dst[i] + lab[j], (double)pv[i][j]);
+  }
+}
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
+  __shared__ double sh[8 * 3 + 8];
+  __shared__ int s_key[TAB_SLOTS];
+  __shared__ double s_val[TAB_SLOTS * 3];
+  __shared__ int s_lab[TAB_SLOTS];
+  __shared__ float s_f[TAB_SLOTS * 4];
+  const int Kc = A.Kc, K = A.K, W = A.W, H = A.H, N = A.N;
+  double* rz = A.cs;
+  double* pap = A.cs + 2 * (size_t)Kc;
+  double* rzn = A.cs + 4 * (size_t)Kc;
+  double* rr = A.cs + 6 * (size_t)Kc;
+  double* bb = A.cs + 8 * (size_t)Kc;
+  double* sx = A.cs + 9 * (size_t)Kc;
+  int* act = A.ci;
+  int* iters = A.ci + 2 * (size_t)Kc;
   int* err = &A.st->err;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
+  const int l8 = threadIdx.x & 7;
+  const double tol2 = A.tol2;
+  if (threadIdx.x < TAB_SLOTS) {
+    s_key[threadIdx.x] = -1;
+    s_val[threadIdx.x * 3] = s_val[threadIdx.x * 3 + 1] = s_val[threadIdx.x * 3 + 2] = 0.0;
+  }
+  __syncthreads();
 
-  // prologue: r = b - A x0, p = z = D^-1 r, per-component r.z, r.r, b.b
-  for (int it = 0; it < nIter; ++it) {
-    const int a = it * nthr + tid;
-    int c = -1;
-    float rz = 0.f, rr = 0.f, bsq = 0.f;
-    if (a < N) {
-      c = A.labels[a];
-      if (c >= 0) {
-        const int u = a % W, v = a / W;
-        Stencil s = load_stencil(A.wfill, a, u, v, W);
-        const float id = A.invd[a];
-        float ra = A.rhs[a] - apply_stencil(s, A.x, a, W, A.x[a]);
-        if (id == 0.f) ra = 0.f;
-        const float z = ra * id;
-        A.r[a] = ra;
-        A.p[a] = z;
-        rz = ra * z;
-        rr = ra * ra;
-        bsq = A.rhs[a] * A.rhs[a];
-      }
+  // ---- prologue: r = b - A x0 on every tile with a valid pixel; rz_{-1}, r^T r, b^T b
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int ul = A.tile_lab[t];
+    if (ul == -2) continue;   // no valid pixel (uniform across the CTA)
+    const G4 g = group_of(t, A.ntx, H, W);
+    int lab[4];
+    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval);
+    const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+    const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+    float xl = __shfl_up_sync(NI_FULL, x4.w, 1), xr = __shfl_down_sync(NI_FULL, x4.x, 1);
+    float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+    if (l8 == 0) {
+      xl = (g.nval > 0 && g.col > 0) ? A.x[g.a - 1] : 0.f;
+      wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
     }
-    seg_add_one<FP64>(rzb0, c, rz);
-    seg_add_one<FP64>(rr0 + Kc, c, rr);
-    seg_add_one<FP64>(bb, c, bsq);
-  }
-  if (!grid_barrier(&A.st->bar, err)) return;
-  for (int c = tid; c < K; c += nthr) {
-    int act = (bb[c] > 0.0) && (rr0[Kc + c] > A.tol2 * bb[c]);
-    A.cflag[c] = act;
-    iters[c] = 0;
-    if (act) atomicAdd(&A.active_cnt[1], 1);
+    if (l8 == 7) xr = (g.nval == 4 && g.col + 4 < W) ? A.x[g.a + 4] : 0.f;
+    const bool up = g.row > 0, dn = g.row + 1 < H;
+    const float4 xu = up ? ldg<ALIGNED>(A.x, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+    const float4 wu4 = up ? ldg<ALIGNED>(A.wd, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+    const float4 xd = dn ? ldg<ALIGNED>(A.x, g.a + W, g.nval) : make_float4(0, 0, 0, 0);
+    float4 r4, p0 = make_float4(0, 0, 0, 0);
+    float pv[3][4];
+    bool on[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xa = f4get(x4, j);
+      const float xR = j < 3 ? f4get(x4, j + 1) : xr, xL = j > 0 ? f4get(x4, j - 1) : xl;
+      const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+      const float ax = f4get(wr4, j) * (xa - xR) + f4get(wd4, j) * (xa - f4get(xd, j)) + wl * (xa - xL) +
+                       f4get(wu4, j) * (xa - f4get(xu, j));
+      on[j] = lab[j] >= 0;
+      float ra = f4get(b4, j) - ax;
+      if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+      f4set(r4, j, ra);
+      pv[0][j] = ra * ra * f4get(id4, j);
+      pv[1][j] = ra * ra;
+      pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
+    }
+    stg<ALIGNED>(A.r, g.a, g.nval, r4);
+    stg<ALIGNED>(A.pb1, g.a, g.nval, p0);
+    double* const dst[3] = {rzn + Kc, rr + Kc, bb};
+    const int key = ul >= 0 ? ul : group_key(lab, on);
+    float v[3];
+    group_values<3>(key, lab, on, pv, dst, v);
+    tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    if (threadIdx.x == 0) {
+      const int pos = atomicAdd(&A.ntl[1], 1);
+      A.tiles[(size_t)A.ntiles + pos] = t;
+    }
   }
   if (!grid_barrier(&A.st->bar, err)) return;
 
-  int it_done = 0;
-  for (int iter = 0; iter < A.maxit; ++iter) {
-    const int k = iter & 1, kp = k ^ 1;
-    if (*(volatile int*)&A.active_cnt[kp] == 0) break;
-    const int* fl = A.cflag + (size_t)k * Kc;
-    // phase A: q = A p, per-component p^T A p
-    for (int it = 0; it < nIter; ++it) {
-      const int a = it * nthr + tid;
-      int c = -1;
-      float pap = 0.f;
-      if (a < N) {
-        int lc = A.labels[a];
-        if (lc >= 0 && fl[lc]) {
-          c = lc;
-          const int u = a % W, v = a / W;
-          Stencil s = load_stencil(A.wfill, a, u, v, W);
-          const float pa = A.p[a];
-          A.q[a] = apply_stencil(s, A.p, a, W, pa);
-          if (s.wr != 0.f) { float d = pa - A.p[a + 1]; pap += s.wr * d * d; }
-          if (s.wd != 0.f) { float d = pa - A.p[a + W]; pap += s.wd * d * d; }
+  for (int k = 0;; ++k) {
+    const int P = k & 1, Q = P ^ 1;
+    const bool last = k >= A.maxit;
+    // ---- phase 1: per-component bookkeeping
+    for (int c = gtid; c < K; c += gthr) {
+      const int wasc = (k > 0) && act[(size_t)Q * Kc + c];
+      const int nowc = (k == 0 || wasc) && bb[c] > 0.0 && rr[(size_t)Q * Kc + c] > tol2 * bb[c];
+      if (last) {
+        if (nowc) {
+          atomicAdd(&A.st->fill_unconv, 1);
+          atomicOr(err, NI_DEV_ERR_FILL_NOCONV);
+        }
+        act[(size_t)P * Kc + c] = 0;
+      } else {
+        act[(size_t)P * Kc + c] = nowc;
+        if (nowc) {
+          iters[c] += 1;
+          rz[(size_t)P * Kc + c] = rzn[(size_t)Q * Kc + c];
         }
       }
-      seg_add_one<FP64>(pap0 + (size_t)k * Kc, c, pap);
+      rzn[(size_t)P * Kc + c] = 0.0;
+      rr[(size_t)P * Kc + c] = 0.0;
+    }
+    // ---- phase 1: tiles active at k-1
+    const int nq = *(volatile int*)&A.ntl[Q];
+    const float* pold = Q ? A.pb1 : A.pb0;
+    float* pnew = P ? A.pb1 : A.pb0;
+    for (int i = blockIdx.x; i < nq; i += gridDim.x) {
+      const int t = A.tiles[(size_t)Q * A.ntiles + i];
+      const int ul = A.tile_lab[t];
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      if (ul >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+      } else {
+        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      }
+      // per-component scalars once per label of the tile: alpha_{k-1} (deferred
+      // x update), beta_k, active at k, active at k-1
+      auto scalars1 = [&](int c, float* o) {
+        const bool was = (k > 0) && act[(size_t)Q * Kc + c];
+        const bool nw = !last && (k == 0 || was) && bb[c] > 0.0 && rr[(size_t)Q * Kc + c] > tol2 * bb[c];
+        const double pp = pap[(size_t)Q * Kc + c], rzo = rz[(size_t)Q * Kc + c];
+        o[0] = (was && pp > 0.0) ? (float)(rzo / pp) : 0.f;
+        o[1] = (nw && k > 0 && rzo > 0.0) ? (float)(rzn[(size_t)Q * Kc + c] / rzo) : 0.f;
+        o[2] = nw ? 1.f : 0.f;
+        o[3] = was ? 1.f : 0.f;
+      };
+      int sl[4];
+      tile_slots(ul, lab, sl, s_lab);
+      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) scalars1(s_lab[threadIdx.x], &s_f[threadIdx.x * 4]);
+      __syncthreads();
+      float alpha[4], beta[4];
+      bool now[4];
+      int any_was = 0, any_now = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+        if (sl[j] >= 0) {
+          o[0] = s_f[sl[j] * 4]; o[1] = s_f[sl[j] * 4 + 1]; o[2] = s_f[sl[j] * 4 + 2]; o[3] = s_f[sl[j] * 4 + 3];
+        } else if (sl[j] == -2) {
+          scalars1(lab[j], o);
+        }
+        alpha[j] = o[0];
+        beta[j] = o[1];
+        now[j] = o[2] != 0.f;
+        any_was |= o[3] != 0.f;
+        any_now |= now[j];
+      }
+      const float4 po4 = ldg<ALIGNED>(pold, g.a, g.nval);
+      if (any_was) {
+        float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
+        x4.x += alpha[0] * po4.x;
+        x4.y += alpha[1] * po4.y;
+        x4.z += alpha[2] * po4.z;
+        x4.w += alpha[3] * po4.w;
+        stg<ALIGNED>(A.x, g.a, g.nval, x4);
+      }
+      if (!__syncthreads_or(any_now)) continue;
+      // p_k at own pixels
+      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      float4 pn;
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        f4set(pn, j, now[j] ? f4get(r4, j) * f4get(id4, j) + beta[j] * f4get(po4, j) : 0.f);
+      // neighbours: left/right through the 8 lanes of a tile row, row ends from memory
+      float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
+      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+      float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+      if (l8 == 0) {
+        const int a = g.a - 1;
+        wl0 = (g.nval > 0 && g.col > 0) ? A.wr[a] : 0.f;
+        pl = (wl0 != 0.f && now[0]) ? A.r[a] * A.invd[a] + beta[0] * pold[a] : 0.f;
+      }
+      if (l8 == 7) {
+        const int a = g.a + 4;
+        pr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f && now[3]) ? A.r[a] * A.invd[a] + beta[3] * pold[a]
+                                                                      : 0.f;
+      }
+      float4 pu = make_float4(0, 0, 0, 0), pd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
+      if (g.row > 0) {
+        wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
+        const float4 ru = ldg<ALIGNED>(A.r, g.a - W, g.nval), iu = ldg<ALIGNED>(A.invd, g.a - W, g.nval);
+        const float4 pu0 = ldg<ALIGNED>(pold, g.a - W, g.nval);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          f4set(pu, j, (now[j] && f4get(wu4, j) != 0.f) ? f4get(ru, j) * f4get(iu, j) + beta[j] * f4get(pu0, j)
+                                                          : 0.f);
+      }
+      if (g.row + 1 < H) {
+        const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
+        const float4 pd0 = ldg<ALIGNED>(pold, g.a + W, g.nval);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          f4set(pd, j, (now[j] && f4get(wd4, j) != 0.f) ? f4get(rd, j) * f4get(idd, j) + beta[j] * f4get(pd0, j)
+                                                          : 0.f);
+      }
+      float4 q4;
+      float pv[1][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float pa = f4get(pn, j);
+        const float pR = j < 3 ? f4get(pn, j + 1) : pr, pL = j > 0 ? f4get(pn, j - 1) : pl;
+        const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+        const float dR = pa - pR, dD = pa - f4get(pd, j);
+        const float qa = f4get(wr4, j) * dR + f4get(wd4, j) * dD + wl * (pa - pL) + f4get(wu4, j) * (pa - f4get(pu, j));
+        f4set(q4, j, now[j] ? qa : 0.f);
+        pv[0][j] = now[j] ? f4get(wr4, j) * dR * dR + f4get(wd4, j) * dD * dD : 0.f;
+      }
+      stg<ALIGNED>(pnew, g.a, g.nval, pn);
+      stg<ALIGNED>(A.q, g.a, g.nval, q4);
+      double* const dst[1] = {pap + (size_t)P * Kc};
+      const int key = ul >= 0 ? ul : group_key(lab, now);
+      float v[1];
+      group_values<1>(key, lab, now, pv, dst, v);
+      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+      if (threadIdx.x == 0) {
+        const int pos = atomicAdd(&A.ntl[P], 1);
+        A.tiles[(size_t)P * A.ntiles + pos] = t;
+      }
     }
     if (!grid_barrier(&A.st->bar, err)) return;
-    // phase B: x += alpha p, r -= alpha q, per-component r.z and r.r
-    for (int c = tid; c < K; c += nthr) pap0[(size_t)kp * Kc + c] = 0.0;
-    if (tid == 0) A.active_cnt[kp] = 0;
-    for (int it = 0; it < nIter; ++it) {
-      const int a = it * nthr + tid;
-      int c = -1;
-      float rz = 0.f, rr = 0.f;
-      if (a < N) {
-        int lc = A.labels[a];
-        if (lc >= 0 && fl[lc]) {
-          c = lc;
-          const double pap = pap0[(size_t)k * Kc + c];
-          const float alpha = pap > 0.0 ? (float)(rzb0[(size_t)k * Kc + c] / pap) : 0.f;
-          const float pa = A.p[a];
-          A.x[a] += alpha * pa;
-          const float ra = A.r[a] - alpha * A.q[a];
-          A.r[a] = ra;
-          rz = ra * ra * A.invd[a];
-          rr = ra * ra;
+    if (*(volatile int*)&A.ntl[P] == 0) break;
+    // ---- phase 2: alpha_k, residual update, per-component r^T D^-1 r and r^T r
+    for (int c = gtid; c < K; c += gthr) pap[(size_t)Q * Kc + c] = 0.0;
+    if (gtid == 0) A.ntl[Q] = 0;
+    const int np = *(volatile int*)&A.ntl[P];
+    for (int i = blockIdx.x; i < np; i += gridDim.x) {
+      const int t = A.tiles[(size_t)P * A.ntiles + i];
+      const int ul = A.tile_lab[t];
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      if (ul >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+      } else {
+        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      }
+      auto scalars2 = [&](int c, float* o) {
+        const bool on = act[(size_t)P * Kc + c];
+        const double pp = pap[(size_t)P * Kc + c];
+        o[0] = (on && pp > 0.0) ? (float)(rz[(size_t)P * Kc + c] / pp) : 0.f;
+        o[1] = on ? 1.f : 0.f;
+      };
+      int sl[4];
+      tile_slots(ul, lab, sl, s_lab);
+      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) scalars2(s_lab[threadIdx.x], &s_f[threadIdx.x * 4]);
+      __syncthreads();
+      float alpha[4];
+      bool on[4];
+      int any = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float o[2] = {0.f, 0.f};
+        if (sl[j] >= 0) {
+          o[0] = s_f[sl[j] * 4]; o[1] = s_f[sl[j] * 4 + 1];
+        } else if (sl[j] == -2) {
+          scalars2(lab[j], o);
         }
+        alpha[j] = o[0];
+        on[j] = o[1] != 0.f;
+        any |= on[j];
       }
-      seg_add_one<FP64>(rzn0 + (size_t)k * Kc, c, rz);
-      seg_add_one<FP64>(rr0 + (size_t)k * Kc, c, rr);
-    }
-    if (!grid_barrier(&A.st->bar, err)) return;
-    // phase D: p = z + beta p; next masks
-    for (int it = 0; it < nIter; ++it) {
-      const int a = it * nthr + tid;
-      if (a < N) {
-        int c = A.labels[a];
-        if (c >= 0 && fl[c]) {
-          const double rzo = rzb0[(size_t)k * Kc + c];
-          const float beta = rzo > 0.0 ? (float)(rzn0[(size_t)k * Kc + c] / rzo) : 0.f;
-          A.p[a] = A.r[a] * A.invd[a] + beta * A.p[a];
-        }
+      float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 q4 = ldg<ALIGNED>(A.q, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      float pv[2][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float ra = f4get(r4, j);
+        if (on[j]) ra -= alpha[j] * f4get(q4, j);
+        f4set(r4, j, ra);
+        pv[0][j] = on[j] ? ra * ra * f4get(id4, j) : 0.f;
+        pv[1][j] = on[j] ? ra * ra : 0.f;
       }
+      if (any) stg<ALIGNED>(A.r, g.a, g.nval, r4);
+      double* const dst[2] = {rzn + (size_t)P * Kc, rr + (size_t)P * Kc};
+      const int key = ul >= 0 ? ul : group_key(lab, on);
+      float v[2];
+      group_values<2>(key, lab, on, pv, dst, v);
+      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
     }
-    for (int c = tid; c < K; c += nthr) {
-      int act = fl[c];
-      int nact = 0;
-      if (act) {
-        rzb0[(size_t)kp * Kc + c] = rzn0[(size_t)k * Kc + c];
-        iters[c] += 1;
-        nact = rr0[(size_t)k * Kc + c] > A.tol2 * bb[c];
-      }
-      A.cflag[(size_t)kp * Kc + c] = nact;
-      rzn0[(size_t)kp * Kc + c] = 0.0;
-      rr0[(size_t)kp * Kc + c] = 0.0;
-      if (nact) atomicAdd(&A.active_cnt[k], 1);
-    }
-    it_done = iter + 1;
     if (!grid_barrier(&A.st->bar, err)) return;
   }
-  // epilogue: statistics and zero mean per component (the gauge of CG from 0)
-  const int kfin = it_done & 1;
-  for (int c = tid; c < K; c += nthr) {
-    atomicMax(&A.st->fill_iters, iters[c]);
-    if (A.cflag[(size_t)kfin * Kc + c]) {
-      atomicAdd(&A.st->fill_unconv, 1);
-      atomicOr(err, NI_DEV_ERR_FILL_NOCONV);
+  // ---- epilogue: zero mean per component (the gauge of CG from 0), statistics
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int ul = A.tile_lab[t];
+    if (ul == -2) continue;
+    const G4 g = group_of(t, A.ntx, H, W);
+    int lab[4];
+    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
+    float pv[2][4];
+    bool on[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      on[j] = lab[j] >= 0;
+      pv[0][j] = on[j] ? f4get(x4, j) : 0.f;
+      pv[1][j] = on[j] ? 1.f : 0.f;
     }
-  }
-  for (int it = 0; it < nIter; ++it) {
-    const int a = it * nthr + tid;
-    int c = (a < N) ? A.labels[a] : -1;
-    double v[2] = {c >= 0 ? (double)A.x[a] : 0.0, c >= 0 ? 1.0 : 0.0};
-    seg_add_d<2>(sx, 1, c, v, (size_t)Kc);   // sum x -> slot 9, count -> slot 10
+    double* const dst[2] = {sx, sx + Kc};
+    const int key = ul >= 0 ? ul : group_key(lab, on);
+    float v[2];
+    group_values<2>(key, lab, on, pv, dst, v);
+    tile_accum<true, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
   }
   if (!grid_barrier(&A.st->bar, err)) return;
-  for (int a = tid; a < N; a += nthr) {
-    int c = A.labels[a];
+  for (int a = gtid; a < N; a += gthr) {
+    const int c = A.labels[a];
     if (c >= 0) {
-      double cnt = sx[(size_t)Kc + c];
+      const double cnt = sx[(size_t)Kc + c];
       if (cnt > 0) A.x[a] = (float)((double)A.x[a] - sx[c] / cnt);
     }
   }
-  for (int c = tid; c < K; c += nthr)
+  for (int c = gtid; c < K; c += gthr) {
+    atomicMax(&A.st->fill_iters, iters[c]);
     if (iters[c] > 0)
       atomicAdd(&A.st->fill_px_iters, (unsigned long long)iters[c] * (unsigned long long)sx[(size_t)Kc + c]);
+  }
 }
 
 ni_status fill_setup_launch(ni_handle* h, cudaStream_t s) {
   const int N = h->N;
-  k_edge_setup<<<grid_px(h, N), 256, 0, s>>>(h->normals, h->mask, h->labels, h->H, h->W, h->persp,
-                                               h->fx, h->fy, h->cx, h->cy, h->omega, h->ntau, h->wfill); NI_COUNT(h);
-  k_diag_rhs<<<grid_px(h, N), 256, 0, s>>>(h->wfill, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+  k_edge_setup<<<grid_px(h, N), 256, 0, s>>>(h->normals, h->mask, h->labels, h->H, h->W, h->persp, h->fx, h->fy,
+                                               h->cx, h->cy, h->omega, h->ntau, h->wr, h->wd); NI_COUNT(h);
+  k_diag_rhs<<<grid_px(h, N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+  k_tile_labels<<<grid_px(h, (long long)h->ntiles * 256), 256, 0, s>>>(h->labels, h->ntiles, h->ntx, h->H, h->W,
+                                                                        h->tile_lab); NI_COUNT(h);
   return ni_cuda_check(h, cudaGetLastError(), "fill setup");
 }
 
@@ -531,8 +940,8 @@ static ni_status plain_solve(ni_handle* h, cudaStream_t s) {
   cudaMemsetAsync(&h->st->cg[0], 0, sizeof(double) * 8, s);
   cudaMemsetAsync(&h->st->bar2, 0, sizeof(GridBar), s);
   const bool f64 = h->cfg.precision == 0;
-  if (f64) k_cg_init<double><<<g, 256, 0, s>>>(h->wfill, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
-  else k_cg_init<float><<<g, 256, 0, s>>>(h->wfill, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
+  if (f64) k_cg_init<double><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
+  else k_cg_init<float><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
   NI_COUNT(h);
   k_cg_init_done<<<1, 1, 0, s>>>(h->st, tol2); NI_COUNT(h);
   ni_status rc = ni_cuda_check(h, cudaGetLastError(), "plain PCG init");
@@ -546,15 +955,14 @@ static ni_status plain_solve(ni_handle* h, cudaStream_t s) {
   cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   const long long launches_before = h->launches;
   for (int i = 0; i < CHUNK; ++i) {
-    if (f64) k_cg_spmv<double><<<g, 256, 0, cs>>>(h->wfill, h->p, h->q, H, W, h->st);
-    else k_cg_spmv<float><<<g, 256, 0, cs>>>(h->wfill, h->p, h->q, H, W, h->st);
+    if (f64) k_cg_spmv<double><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
+    else k_cg_spmv<float><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
     NI_COUNT(h);
     if (f64) k_cg_update<double><<<g, 256, 0, cs>>>(h->invd, h->p, h->q, h->x, h->r, N, h->st);
     else k_cg_update<float><<<g, 256, 0, cs>>>(h->invd, h->p, h->q, h->x, h->r, N, h->st);
     NI_COUNT(h);
     k_cg_dir<<<g, 256, 0, cs>>>(h->invd, h->r, h->p, N, h->st, counter, tol2, maxit); NI_COUNT(h);
   }
-
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   const long long per_chunk = h->launches - launches_before;
   h->launches = launches_before;
@@ -586,27 +994,35 @@ __global__ void k_plain_stats(DevState* st, int maxit, double tol2) {
   }
 }
 
+template <bool FP64, bool AL>
+static void* pcg_fn() {
+  return (void*)k_pcg_tiles<FP64, AL>;
+}
+
 static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   const bool f64 = h->cfg.precision == 0;
-  void* fn = f64 ? (void*)k_pcg_batched<true> : (void*)k_pcg_batched<false>;
+  const bool al = (h->W % 4) == 0;
+  void* fn = f64 ? (al ? pcg_fn<true, true>() : pcg_fn<true, false>())
+                 : (al ? pcg_fn<false, true>() : pcg_fn<false, false>());
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NI_TILE_THREADS, 0);
   if (per_sm < 1) return ni_fail(h, NI_ERR_CUDA, "batched PCG: kernel cannot be resident");
-  int grid = h->num_sms * std::min(per_sm, 4);
-  long long need = ((long long)h->N + 255) / 256;
-  if (grid > need) grid = (int)std::max(1LL, need);
+  const int want = h->cfg.tile_w > 0 ? h->cfg.tile_w : 4;   // CTAs per SM (tuned)
+  int grid = h->num_sms * std::min(per_sm, want);
+  grid = std::max(1, std::min(grid, h->ntiles));
   cudaMemsetAsync(h->cacc, 0, sizeof(double) * 11 * (size_t)h->Kcap, s);
+  cudaMemsetAsync(h->cflag, 0, sizeof(int) * 3 * (size_t)h->Kcap, s);
   cudaMemsetAsync(&h->st->bar, 0, sizeof(GridBar), s);
-  int* active_cnt = reinterpret_cast<int*>(&h->st->bar2);
-  cudaMemsetAsync(active_cnt, 0, sizeof(GridBar), s);
+  int* ntl = reinterpret_cast<int*>(&h->st->bar2);
+  cudaMemsetAsync(ntl, 0, sizeof(GridBar), s);
   PcgArgs a;
-  a.wfill = h->wfill; a.invd = h->invd; a.rhs = h->b; a.labels = h->labels;
-  a.x = h->x; a.r = h->r; a.p = h->p; a.q = h->q;
-  a.cacc = h->cacc; a.cflag = h->cflag; a.st = h->st; a.active_cnt = active_cnt;
-  a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kcap = h->Kcap;
+  a.wr = h->wr; a.wd = h->wd; a.invd = h->invd; a.rhs = h->b; a.labels = h->labels; a.tile_lab = h->tile_lab;
+  a.x = h->x; a.r = h->r; a.pb0 = h->p; a.pb1 = h->p2; a.q = h->q;
+  a.cs = h->cacc; a.ci = h->cflag; a.tiles = h->tiles; a.ntl = ntl; a.st = h->st;
+  a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
   void* args[] = {&a};
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);
   NI_COUNT(h);
   return ni_cuda_check(h, e, "batched PCG launch");
 }
@@ -616,9 +1032,9 @@ ni_status fill_solve_launch(ni_handle* h, cudaStream_t s) {
   if (rc != NI_OK) return rc;
   for (int sweep = 0; sweep < std::max(1, h->cfg.n_fill_irls); ++sweep) {
     if (sweep > 0) {
-      k_fill_reweight<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp,
-                                                        h->fx, h->fy, (float)h->cfg.k, h->wfill); NI_COUNT(h);
-      k_diag_rhs<<<grid_px(h, h->N), 256, 0, s>>>(h->wfill, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+      k_fill_reweight<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp, h->fx,
+                                                        h->fy, (float)h->cfg.k, h->wr, h->wd); NI_COUNT(h);
+      k_diag_rhs<<<grid_px(h, h->N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
       rc = project_rhs(h, h->b, s);
       if (rc != NI_OK) return rc;
     }

@@ -74,6 +74,9 @@ struct ni_handle {
   int num_sms = 0;
   int H = 0, W = 0;
   int N = 0;
+  int Npad = 0;                // N rounded up to a multiple of 1024 (allocation size)
+  int ntiles = 0;              // 32 x 32 tiles of the batched PCG
+  int ntx = 0;                 // tiles per tile row
   double cos_theta = 2.0;   // > 1 keeps no edge (theta_c = None)
   float fx = 1, fy = 1, cx = 0, cy = 0;
   int persp = 1;
@@ -87,7 +90,8 @@ struct ni_handle {
   int32_t* parent = nullptr;   // union-find scratch / previous labels
   float2* omega = nullptr;     // omega~_{b->a} of the right (x) and down (y) edge
   float* ntau = nullptr;       // n_a . tau_a (n_az for orthographic)
-  float2* wfill = nullptr;     // combined fill weights of the right / down edge
+  float* wr = nullptr;         // combined fill weight of the edge to the right
+  float* wd = nullptr;         // combined fill weight of the edge below
   float* invd = nullptr;       // 1 / Jacobi diagonal (0 where the diagonal is 0)
   float* x = nullptr;          // log-depth relative to the component offset
   float* r = nullptr;
@@ -95,6 +99,9 @@ struct ni_handle {
   float* p2 = nullptr;
   float* q = nullptr;
   float* b = nullptr;          // right-hand side of the fill normal equations
+
+  int* tile_lab = nullptr;     // uniform label of each tile or -1
+  int* tiles = nullptr;        // active tile lists of the batched PCG [2 * ntiles]
 
   // scan scratch
   int* blk = nullptr;          // block partial sums (NI_SCAN_BLOCKS + 1)
@@ -158,6 +165,10 @@ struct ni_handle {
 // ----------------------------------------------------------------------------
 // launch geometry
 // ----------------------------------------------------------------------------
+#define NI_TILE_PX 1024
+#define NI_TILE_W 32
+#define NI_TILE_H 32
+#define NI_TILE_THREADS 256
 #define NI_SCAN_BLOCKS 1024
 #define NI_SCAN_THREADS 512
 #define NI_SORT_BLOCKS 256
