@@ -194,7 +194,7 @@ extern "C" ni_status ni_create(const ni_config* cfg, ni_handle** out) {
   if (e == cudaSuccess) e = dalloc(&h->q, NP);
   if (e == cudaSuccess) e = dalloc(&h->b, NP);
   if (e == cudaSuccess) e = dalloc(&h->tile_lab, (size_t)h->ntiles);
-  if (e == cudaSuccess) e = dalloc(&h->tiles, 2 * (size_t)h->ntiles);
+  if (e == cudaSuccess) e = dalloc(&h->tiles, 4 * (size_t)h->ntiles);
   // padding pixels beyond N: label -1, weights and vectors 0 (never written later)
   if (e == cudaSuccess) e = cudaMemset(h->labels, 0xff, NP * sizeof(int32_t));
   float* zero_planes[] = {h->wr, h->wd, h->invd, h->x, h->r, h->p, h->p2, h->q, h->b};

@@ -391,7 +391,7 @@ struct PcgArgs {
   float* q;
   double* cs;
   int* ci;
-  int* tiles;      // [2][ntiles]
+  int2* tiles;     // [2][ntiles] (tile, uniform label)
   int* ntl;        // [2] list lengths
   DevState* st;
   int N, H, W, K, Kc, ntiles, ntx, maxit;
@@ -445,15 +445,17 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2)
   hi = s;
 }
 
+// Warp total as a float pair (hi, lo); lo = 0 without compensation.  Callers
+// convert to double only in the lane that uses the result.
 template <bool COMP>
-__device__ __forceinline__ double warp_total(float v) {
+__device__ __forceinline__ float2 warp_total(float v) {
   if (COMP) {
     float hi = v, lo = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ff_add(hi, lo, __shfl_xor_sync(NI_FULL, hi, o), __shfl_xor_sync(NI_FULL, lo, o));
-    return (double)hi + (double)lo;
+    return make_float2(hi, lo);
   }
-  return (double)warp_sum_f(v);
+  return make_float2(warp_sum_f(v), 0.f);
 }
 
 // Add NV per-thread values into dst[v][label].  `key` is the label all of the
@@ -466,12 +468,12 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
                                            int* s_key, double* s_val, double* sh) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (ul >= 0) {
-    double w[NV];
+    float2 w[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) w[j] = warp_total<COMP>(v[j]);
     if (lane == 0)
 #pragma unroll
-      for (int j = 0; j < NV; ++j) sh[wid * NV + j] = w[j];
+      for (int j = 0; j < NV; ++j) sh[wid * NV + j] = (double)w[j].x + (double)w[j].y;
     __syncthreads();
     if (threadIdx.x < NV) {
       double t = 0.0;
@@ -488,7 +490,7 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
   const bool tail = (lane == 31) || (next != key);
   const unsigned heads = __ballot_sync(NI_FULL, head);
   const int my_head = 31 - __clz(heads & ((2u << lane) - 1u));
-  double acc[NV];
+  float2 acc[NV];
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     float hi = v[j], lo = 0.f;
@@ -501,7 +503,7 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
         else hi += h2;
       }
     }
-    acc[j] = (double)hi + (double)lo;
+    acc[j] = make_float2(hi, lo);
   }
   if (tail && key >= 0) {
     int h = key & (TAB_SLOTS - 1), slot = -1;
@@ -512,9 +514,10 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
     }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
-      if (acc[j] == 0.0) continue;
-      if (slot >= 0) atomicAdd(&s_val[slot * 3 + j], acc[j]);
-      else atomicAdd(dst[j] + key, acc[j]);
+      const double t = (double)acc[j].x + (double)acc[j].y;
+      if (t == 0.0) continue;
+      if (slot >= 0) atomicAdd(&s_val[slot * 3 + j], t);
+      else atomicAdd(dst[j] + key, t);
     }
   }
   __syncthreads();
@@ -595,7 +598,10 @@ __device__ __forceinline__ void group_values(int key, const int (&lab)[4], const
 }
 
 template <bool COMP, bool ALIGNED>
-__global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
+#ifndef NI_PCG_MIN_BLOCKS
+#define NI_PCG_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(NI_TILE_THREADS, NI_PCG_MIN_BLOCKS) k_pcg_tiles(PcgArgs A) {
   __shared__ double sh[8 * 3 + 8];
   __shared__ int s_key[TAB_SLOTS];
   __shared__ double s_val[TAB_SLOTS * 3];
@@ -668,7 +674,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
     tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
     if (threadIdx.x == 0) {
       const int pos = atomicAdd(&A.ntl[1], 1);
-      A.tiles[(size_t)A.ntiles + pos] = t;
+      A.tiles[(size_t)A.ntiles + pos] = make_int2(t, ul);
     }
   }
   if (!grid_barrier(&A.st->bar, err)) return;
@@ -701,8 +707,8 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
     const float* pold = Q ? A.pb1 : A.pb0;
     float* pnew = P ? A.pb1 : A.pb0;
     for (int i = blockIdx.x; i < nq; i += gridDim.x) {
-      const int t = A.tiles[(size_t)Q * A.ntiles + i];
-      const int ul = A.tile_lab[t];
+      const int2 te = A.tiles[(size_t)Q * A.ntiles + i];
+      const int t = te.x, ul = te.y;
       const G4 g = group_of(t, A.ntx, H, W);
       int lab[4];
       if (ul >= 0) {
@@ -722,6 +728,11 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
         o[2] = nw ? 1.f : 0.f;
         o[3] = was ? 1.f : 0.f;
       };
+      // own-pixel operands, issued before the scalar cache so their latency overlaps it
+      const float4 po4 = ldg<ALIGNED>(pold, g.a, g.nval);
+      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
+      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
       int sl[4];
       tile_slots(ul, lab, sl, s_lab);
       if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) scalars1(s_lab[threadIdx.x], &s_f[threadIdx.x * 4]);
@@ -743,9 +754,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
         any_was |= o[3] != 0.f;
         any_now |= now[j];
       }
-      const float4 po4 = ldg<ALIGNED>(pold, g.a, g.nval);
       if (any_was) {
-        float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
         x4.x += alpha[0] * po4.x;
         x4.y += alpha[1] * po4.y;
         x4.z += alpha[2] * po4.z;
@@ -754,14 +763,12 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
       }
       if (!__syncthreads_or(any_now)) continue;
       // p_k at own pixels
-      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
       float4 pn;
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         f4set(pn, j, now[j] ? f4get(r4, j) * f4get(id4, j) + beta[j] * f4get(po4, j) : 0.f);
       // neighbours: left/right through the 8 lanes of a tile row, row ends from memory
       float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
-      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
       float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
       if (l8 == 0) {
         const int a = g.a - 1;
@@ -812,7 +819,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
       tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
       if (threadIdx.x == 0) {
         const int pos = atomicAdd(&A.ntl[P], 1);
-        A.tiles[(size_t)P * A.ntiles + pos] = t;
+        A.tiles[(size_t)P * A.ntiles + pos] = make_int2(t, ul);
       }
     }
     if (!grid_barrier(&A.st->bar, err)) return;
@@ -822,8 +829,8 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
     if (gtid == 0) A.ntl[Q] = 0;
     const int np = *(volatile int*)&A.ntl[P];
     for (int i = blockIdx.x; i < np; i += gridDim.x) {
-      const int t = A.tiles[(size_t)P * A.ntiles + i];
-      const int ul = A.tile_lab[t];
+      const int2 te = A.tiles[(size_t)P * A.ntiles + i];
+      const int t = te.x, ul = te.y;
       const G4 g = group_of(t, A.ntx, H, W);
       int lab[4];
       if (ul >= 0) {
@@ -832,6 +839,8 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
       } else {
         ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
       }
+      float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 q4 = ldg<ALIGNED>(A.q, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
       auto scalars2 = [&](int c, float* o) {
         const bool on = act[(size_t)P * Kc + c];
         const double pp = pap[(size_t)P * Kc + c];
@@ -857,8 +866,6 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_pcg_tiles(PcgArgs A) {
         on[j] = o[1] != 0.f;
         any |= on[j];
       }
-      float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
-      const float4 q4 = ldg<ALIGNED>(A.q, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
       float pv[2][4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -1018,7 +1025,7 @@ static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   PcgArgs a;
   a.wr = h->wr; a.wd = h->wd; a.invd = h->invd; a.rhs = h->b; a.labels = h->labels; a.tile_lab = h->tile_lab;
   a.x = h->x; a.r = h->r; a.pb0 = h->p; a.pb1 = h->p2; a.q = h->q;
-  a.cs = h->cacc; a.ci = h->cflag; a.tiles = h->tiles; a.ntl = ntl; a.st = h->st;
+  a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
   void* args[] = {&a};

@@ -101,7 +101,7 @@ struct ni_handle {
   float* b = nullptr;          // right-hand side of the fill normal equations
 
   int* tile_lab = nullptr;     // uniform label of each tile or -1
-  int* tiles = nullptr;        // active tile lists of the batched PCG [2 * ntiles]
+  int* tiles = nullptr;        // active tile lists of the batched PCG [2][ntiles] x (tile, label)
 
   // scan scratch
   int* blk = nullptr;          // block partial sums (NI_SCAN_BLOCKS + 1)
