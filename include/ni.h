@@ -88,7 +88,8 @@ typedef struct {
                                1: one persistent launch, per-component step lengths and
                                   convergence masks */
   int use_graph;            /* capture the relative-scale loop in a CUDA graph */
-  int warm_start;           /* 1: x0 of the fill from the loaded CNN (ni_load_net) */
+  int warm_start;           /* 1: x0 of the fill from the loaded CNN (ni_load_net), scaled per
+                               component by its energy-optimal factor; needs batched = 1 */
   int hard_outliers;        /* 1: hard W^out variant (supplementary, outlier ablation) */
   int validate;             /* 1: check normals (unit length within 1e-3, n.tau != 0) */
   int tile_w, tile_h;       /* stencil tile shape (0 = tuned default) */
@@ -111,6 +112,7 @@ typedef struct {
   double ms_fill_solve;     /* device time of the fill PCG launch(es) alone */
   int64_t fill_px_iters;    /* sum over components of pixels x PCG iterations */
   int64_t kernel_launches;  /* kernels this call launched (graph nodes included) */
+  int32_t warm_fallbacks;   /* components whose energy-optimal warm-start scale was 0 (cold start) */
 } ni_stats;
 
 /* Default configuration for an H x W map (Algorithm 1's defaults of the paper's

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <string>
 
+#include "../../include/ni_cnn.h"
 #include "ni_internal.cuh"
 
 ni_status ni_fail(ni_handle* h, ni_status s, const std::string& msg) {
@@ -81,6 +82,7 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->n_fill_irls < 1 || c->n_fill_irls > 16) { why = "n_fill_irls in [1, 16]"; return NI_ERR_INVALID_ARG; }
   if (c->precision != 0 && c->precision != 1) { why = "precision must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (!(c->dE_max >= 0)) { why = "dE_max must be >= 0"; return NI_ERR_INVALID_ARG; }
+  if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;
 }
 
@@ -105,7 +107,7 @@ ni_status ensure_component_capacity(ni_handle* h, int K) {
   size_t k = (size_t)need;
   if (e == cudaSuccess) e = dalloc(&h->soff, k);
   if (e == cudaSuccess) e = dalloc(&h->soff2, k);
-  if (e == cudaSuccess) e = dalloc(&h->cacc, 11 * k + 16);
+  if (e == cudaSuccess) e = dalloc(&h->cacc, 14 * k + 16);
   if (e == cudaSuccess) e = dalloc(&h->cflag, 3 * k);
   if (e == cudaSuccess) e = dalloc(&h->kparent, k);
   if (e == cudaSuccess) e = dalloc(&h->kmap, k);
@@ -224,6 +226,8 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   dfree(h->invd); dfree(h->x); dfree(h->r); dfree(h->p); dfree(h->p2); dfree(h->q); dfree(h->b);
   dfree(h->blk); dfree(h->d_count); dfree(h->radix_hist); dfree(h->st);
   dfree(h->in_normals); dfree(h->in_mask); dfree(h->out_depth);
+  dfree(h->tile_in); dfree(h->tile_out);
+  if (h->net) ni_cnn_destroy(h->net);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (int i = 0; i < 8; ++i)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -293,12 +297,17 @@ extern "C" ni_status ni_seed_components(ni_handle* h, const float* normals, cons
 extern "C" ni_status ni_solve_components(ni_handle* h, float* logdepth_out, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
   if (h->stage < 1) return ni_fail(h, NI_ERR_STATE, "ni_solve_components before ni_seed_components");
-  if (h->cfg.warm_start) return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
+  if (h->cfg.warm_start && !h->net)
+    return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
   cudaStream_t s = (cudaStream_t)stream;
   h->err.clear();
   ni_status rc = fill_setup_launch(h, s);
   if (rc != NI_OK) return rc;
   cudaMemsetAsync(h->x, 0, sizeof(float) * h->N, s);
+  if (h->cfg.warm_start) {
+    rc = warm_start_launch(h, s);
+    if (rc != NI_OK) return rc;
+  }
   cudaMemsetAsync(h->soff, 0, sizeof(double) * h->Kcap, s);
   rc = fill_solve_launch(h, s);
   if (rc != NI_OK) return rc;
@@ -471,6 +480,7 @@ extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint
     stats->ms_fill_solve = h->ms_fill_solve;
     stats->fill_px_iters = (int64_t)d->fill_px_iters;
     stats->kernel_launches = h->launches - launches0;
+    stats->warm_fallbacks = d->warm_fallbacks;
   }
   if (fill_rc != NI_OK) return ni_fail(h, fill_rc, fill_msg);
   return NI_OK;
@@ -507,8 +517,3 @@ extern "C" ni_status ni_get_logdepth(ni_handle* h, float* out, ni_stream_t strea
   return ni_cuda_check(h, cudaStreamSynchronize(s), "log-depth export");
 }
 
-extern "C" ni_status ni_load_net(ni_handle* h, const char* path) {
-  if (!h) return NI_ERR_INVALID_ARG;
-  (void)path;
-  return ni_fail(h, NI_ERR_INVALID_ARG, "the learned warm start is not available in this build");
-}

@@ -29,8 +29,9 @@
 //           a step length, direction update and convergence mask per component,
 //           working on a list of 1024-pixel tiles that still hold an active
 //           component.
-// Both start from x0 (0 or the warm start), project the right-hand side and the
-// result to zero mean per component (the gauge CG from 0 reaches).
+// Both start from x0 = 0, the batched one also from the warm start, which it
+// first scales per component by the minimiser of the energy along x0; both
+// project the right-hand side and the result to zero mean per component.
 #include <algorithm>
 #include <vector>
 
@@ -362,7 +363,8 @@ __global__ void k_cg_dir(const float* __restrict__ invd, const float* __restrict
 // batched persistent Jacobi-PCG over active tiles
 // ---------------------------------------------------------------------------
 // Per-component state (doubles, Kc each): 0,1 rz of iteration parity; 2,3 p^T A p;
-// 4,5 rz_new; 6,7 r^T r; 8 b^T b; 9 sum x; 10 count.
+// 4,5 rz_new; 6,7 r^T r; 8 b^T b; 9 sum x; 10 count; with a warm start also
+// 11 x0^T b, 12 x0^T A x0, 13 the component's scale of x0.
 // Per-component ints: [0, 2 Kc) active flag per parity; [2 Kc, 3 Kc) iterations.
 // Iteration k (parity P = k & 1, Q = P ^ 1), on the tiles of list Q (active at k-1):
 //  phase 1: deferred update x += alpha_{k-1} p_{k-1}; for components still active
@@ -395,6 +397,7 @@ struct PcgArgs {
   int* ntl;        // [2] list lengths
   DevState* st;
   int N, H, W, K, Kc, ntiles, ntx, maxit;
+  int warm;        // x0 comes from the warm start: scale it per component (energy-optimal)
   double tol2;
 };
 
@@ -614,6 +617,9 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, NI_PCG_MIN_BLOCKS) k_pcg_tile
   double* rr = A.cs + 6 * (size_t)Kc;
   double* bb = A.cs + 8 * (size_t)Kc;
   double* sx = A.cs + 9 * (size_t)Kc;
+  double* xb = A.cs + 11 * (size_t)Kc;
+  double* xax = A.cs + 12 * (size_t)Kc;
+  double* alpha = A.cs + 13 * (size_t)Kc;
   int* act = A.ci;
   int* iters = A.ci + 2 * (size_t)Kc;
   int* err = &A.st->err;
@@ -661,13 +667,18 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, NI_PCG_MIN_BLOCKS) k_pcg_tile
       float ra = f4get(b4, j) - ax;
       if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
       f4set(r4, j, ra);
-      pv[0][j] = ra * ra * f4get(id4, j);
-      pv[1][j] = ra * ra;
+      if (A.warm) {   // x0^T b and x0^T A x0 of the warm start
+        pv[0][j] = on[j] ? xa * f4get(b4, j) : 0.f;
+        pv[1][j] = on[j] ? xa * ax : 0.f;
+      } else {
+        pv[0][j] = ra * ra * f4get(id4, j);
+        pv[1][j] = ra * ra;
+      }
       pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
     }
     stg<ALIGNED>(A.r, g.a, g.nval, r4);
     stg<ALIGNED>(A.pb1, g.a, g.nval, p0);
-    double* const dst[3] = {rzn + Kc, rr + Kc, bb};
+    double* const dst[3] = {A.warm ? xb : rzn + Kc, A.warm ? xax : rr + Kc, bb};
     const int key = ul >= 0 ? ul : group_key(lab, on);
     float v[3];
     group_values<3>(key, lab, on, pv, dst, v);
@@ -678,6 +689,48 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, NI_PCG_MIN_BLOCKS) k_pcg_tile
     }
   }
   if (!grid_barrier(&A.st->bar, err)) return;
+  if (A.warm) {
+    // Warm start: scale the start vector per component by the minimiser of the
+    // energy of alpha * x0, alpha = x0^T b / x0^T A x0, so that the start's
+    // A-norm error never exceeds that of x0 = 0 (alpha = 0 is the cold start).
+    for (int c = gtid; c < K; c += gthr) {
+      const double al = (xax[c] > 0.0 && xb[c] > 0.0) ? xb[c] / xax[c] : 0.0;
+      alpha[c] = al;
+      if (al == 0.0 && bb[c] > 0.0) atomicAdd(&A.st->warm_fallbacks, 1);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+    for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+      const int ul = A.tile_lab[t];
+      if (ul == -2) continue;
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      float pv[2][4];
+      bool on[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        on[j] = lab[j] >= 0;
+        const float al = on[j] ? (float)alpha[lab[j]] : 0.f;
+        f4set(x4, j, al * f4get(x4, j));
+        // r = b - A (al x0) = (1 - al) b + al (b - A x0)
+        float ra = (1.f - al) * f4get(b4, j) + al * f4get(r4, j);
+        if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+        f4set(r4, j, ra);
+        pv[0][j] = ra * ra * f4get(id4, j);
+        pv[1][j] = ra * ra;
+      }
+      stg<ALIGNED>(A.x, g.a, g.nval, x4);
+      stg<ALIGNED>(A.r, g.a, g.nval, r4);
+      double* const dst[2] = {rzn + Kc, rr + Kc};
+      const int key = ul >= 0 ? ul : group_key(lab, on);
+      float v[2];
+      group_values<2>(key, lab, on, pv, dst, v);
+      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+  }
 
   for (int k = 0;; ++k) {
     const int P = k & 1, Q = P ^ 1;
@@ -1017,7 +1070,7 @@ static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   const int want = h->cfg.tile_w > 0 ? h->cfg.tile_w : 4;   // CTAs per SM (tuned)
   int grid = h->num_sms * std::min(per_sm, want);
   grid = std::max(1, std::min(grid, h->ntiles));
-  cudaMemsetAsync(h->cacc, 0, sizeof(double) * 11 * (size_t)h->Kcap, s);
+  cudaMemsetAsync(h->cacc, 0, sizeof(double) * 14 * (size_t)h->Kcap, s);
   cudaMemsetAsync(h->cflag, 0, sizeof(int) * 3 * (size_t)h->Kcap, s);
   cudaMemsetAsync(&h->st->bar, 0, sizeof(GridBar), s);
   int* ntl = reinterpret_cast<int*>(&h->st->bar2);
@@ -1028,6 +1081,7 @@ static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
+  a.warm = h->cfg.warm_start ? 1 : 0;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);
   NI_COUNT(h);

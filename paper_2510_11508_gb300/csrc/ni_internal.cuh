@@ -53,7 +53,7 @@ struct DevState {
   int cg_it;       // plain fill PCG: iterations
   int gate;        // merge kernels of this iteration run (1) or not (0)
   int n_valid;     // valid pixels of the map
-  int pad0;
+  int warm_fallbacks;  // components whose warm start was scaled to zero (cold start)
   unsigned long long fill_px_iters;  // sum over components of size x PCG iterations
   double E[NI_MAX_T + 1];  // E[0] = eps, E[t] after iteration t
   double cg[8];            // plain fill PCG scalars
@@ -67,6 +67,8 @@ struct DevState {
 #define CG_PAP 2
 #define CG_RR 3
 #define CG_BB 4
+
+struct ni_cnn;
 
 struct ni_handle {
   ni_config cfg;
@@ -156,6 +158,11 @@ struct ni_handle {
   cudaGraphExec_t scale_graph = nullptr;
   long long graph_key[6] = {-1, -1, -1, -1, -1, -1};
 
+  // learned warm start (ni_load_net)
+  ni_cnn* net = nullptr;
+  float* tile_in = nullptr;
+  float* tile_out = nullptr;
+
   // device copies for ni_integrate_host
   float4* in_normals = nullptr;
   uint8_t* in_mask = nullptr;
@@ -200,6 +207,9 @@ int scale_cg_grid(ni_handle* h);
 void merge_gate_launch(ni_handle* h, int tgate, int force, cudaStream_t s);
 ni_status ensure_edge_capacity(ni_handle* h, int nE);
 ni_status ensure_component_capacity(ni_handle* h, int K);
+
+// ni_cnn.cu
+ni_status warm_start_launch(ni_handle* h, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // device helpers

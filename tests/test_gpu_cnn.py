@@ -1,0 +1,127 @@
+"""Learned warm start: the BF16 tensor-core network kernels against the FP64
+oracle with the same bf16 rounding points, its training loop, its input tiling,
+its edge-weight targets, and the warm-started fill against the cold start."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import cnn_oracle as CO
+from paper_2510_11508_gb300 import cnn, ni
+from synth import make_workload
+from synth import generators as G
+
+from gpu_util import dev, integrator
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(B=2, T=16, seed=0):
+    rng = np.random.default_rng(seed)
+    S = T + 2 * CO.HALO
+    x = rng.normal(0, 0.5, (B, S, S, 4)).astype(np.float32)
+    x[..., 3] = (rng.uniform(size=(B, S, S)) > 0.1)
+    tz = rng.normal(0, 1, (B, T, T)).astype(np.float32)
+    tl = rng.integers(-1, 3, (B, T, T)).astype(np.int32)
+    tw = rng.uniform(0, 1, (B, T, T, 4)).astype(np.float32)
+    return x, tz, tl, tw
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_forward_matches_oracle():
+    x, *_ = _batch()
+    net = cnn.Net(4, 16, seed=1)
+    p = net.get_params().astype(np.float64)
+    out = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref, _ = CO.forward(p, x.astype(np.float64), quantize=True)
+    err = _rel(out, ref)
+    print("forward rel err", err)
+    assert err < 5e-3
+
+
+def test_loss_and_gradients_match_oracle():
+    x, tz, tl, tw = _batch(seed=1)
+    net = cnn.Net(4, 16, seed=2)
+    p = net.get_params().astype(np.float64)
+    t = [torch.from_numpy(a).cuda() for a in (x, tz, tl, tw)]
+    (loss, ld, lw), g = net.loss_grad(*t, w_weight=0.3)
+    (rloss, rld, rlw), rg = CO.backward(p, x.astype(np.float64), tz.astype(np.float64), tl, tw.astype(np.float64),
+                                        0.3, quantize=True)
+    print("loss", loss, rloss, "grad rel err", _rel(g, rg))
+    assert abs(loss - rloss) <= 1e-3 * abs(rloss)
+    assert _rel(g, rg) < 2e-2
+    # per layer (weights and biases of every layer carry gradient)
+    o = 0
+    for ci, co in CO.LAYERS:
+        n = 9 * ci * co + co
+        assert _rel(g[o:o + n], rg[o:o + n]) < 5e-2
+        o += n
+
+
+def test_training_reduces_loss():
+    x, tz, tl, tw = _batch(B=4, seed=3)
+    net = cnn.Net(4, 16, seed=3)
+    t = [torch.from_numpy(a).cuda() for a in (x, tz, tl, tw)]
+    first = net.train_step(*t, lr=1e-3)[0]
+    for _ in range(60):
+        last = net.train_step(*t, lr=1e-3)[0]
+    assert last < 0.7 * first, (first, last)
+
+
+def test_make_tiles_halo():
+    nrm, mask, cam = G.random_normal_field(40, 37, seed=2)
+    n, m = dev(nrm, mask)
+    tiles = cnn.make_tiles(n, m, 16).cpu().numpy()
+    assert tiles.shape == (9, 28, 28, 4)
+    ref = np.zeros((48 + 12 + 12, 48 + 12 + 12, 4), np.float32)
+    ref[6:46, 6:43, :3] = np.where(mask[..., None] > 0, nrm[..., :3], 0)
+    ref[6:46, 6:43, 3] = mask
+    for t in range(9):
+        ty, tx = divmod(t, 3)
+        np.testing.assert_array_equal(tiles[t], ref[16 * ty:16 * ty + 28, 16 * tx:16 * tx + 28])
+
+
+def test_edge_targets_match_oracle_bini_weights():
+    w = make_workload("c3_small")
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    rng = np.random.default_rng(0)
+    z = rng.normal(0, 1e-3, (H, W)).astype(np.float32)
+    out = cnn.edge_targets(n, m, torch.from_numpy(z).cuda(), w.camera).cpu().numpy()
+    cam = O.Camera.from_dict(w.camera)
+    valid = w.mask.reshape(-1).astype(bool)
+    zz = z.reshape(-1).astype(np.float64)
+    for dirn, (du, dv) in enumerate([(1, 0), (0, 1), (-1, 0), (0, -1)]):
+        v, u = np.nonzero(w.mask)
+        ub, vb = u + du, v + dv
+        ok = (ub >= 0) & (ub < W) & (vb >= 0) & (vb < H)
+        a = (v * W + u)[ok]
+        b = (vb * W + ub)[ok]
+        ok2 = valid[b]
+        a, b = a[ok2], b[ok2]
+        d = np.full(len(a), 0 if du != 0 else 1)
+        gam = O.gamma(w.normals, cam, H, W, a, d)
+        ref = O.bini_weight(zz, gam, a, b, d, H, W, valid, 2.0) / (gam * gam)
+        got = out.reshape(-1, 4)[a, dirn]
+        np.testing.assert_allclose(got, ref, atol=2e-3)
+
+
+def test_warm_start_gives_the_cold_start_answer(tmp_path):
+    w = make_workload("c2")
+    H, W = w.mask.shape
+    net = cnn.Net(16, 64, seed=5)
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    n, m = dev(w.normals, w.mask)
+    cold = integrator(H, W, w.camera, w.params)
+    d0, l0, s0 = cold.integrate(n, m)
+    warm = integrator(H, W, w.camera, w.params, warm_start=1)
+    warm.load_net(path)
+    d1, l1, s1 = warm.integrate(n, m)
+    assert np.array_equal(l0.cpu().numpy(), l1.cpu().numpy())
+    err = O.aligned_rel_rmse(d1.cpu().numpy(), d0.cpu().numpy(), w.mask, 1)
+    print("warm vs cold rel err", err, "iters", s0["fill_iters"], s1["fill_iters"])
+    assert err < 1e-4
