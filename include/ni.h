@@ -93,6 +93,11 @@ typedef struct {
   int hard_outliers;        /* 1: hard W^out variant (supplementary, outlier ablation) */
   int validate;             /* 1: check normals (unit length within 1e-3, n.tau != 0) */
   int tile_w, tile_h;       /* stencil tile shape (0 = tuned default) */
+  int precond;              /* preconditioner of the batched fill: 0 Jacobi, 1 one symmetric
+                               V-cycle of aggregation multigrid on the pixel grid */
+  double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.67) */
+  double mg_correction;     /* scale of the coarse-grid correction (0: 1.5) */
+  int mg_cta_cells;         /* levels of at most this many cells run in one CTA (0: 4096) */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

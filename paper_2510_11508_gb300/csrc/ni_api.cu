@@ -62,6 +62,10 @@ extern "C" void ni_config_default(ni_config* c, int H, int W) {
   c->batched = 1;
   c->use_graph = 1;
   c->warm_start = 0;
+  c->precond = 0;
+  c->mg_omega = 0;
+  c->mg_correction = 0;
+  c->mg_cta_cells = 0;
   c->hard_outliers = 0;
   c->validate = 1;
 }
@@ -82,6 +86,10 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->n_fill_irls < 1 || c->n_fill_irls > 16) { why = "n_fill_irls in [1, 16]"; return NI_ERR_INVALID_ARG; }
   if (c->precision != 0 && c->precision != 1) { why = "precision must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (!(c->dE_max >= 0)) { why = "dE_max must be >= 0"; return NI_ERR_INVALID_ARG; }
+  if (c->precond != 0 && c->precond != 1) { why = "precond must be 0 or 1"; return NI_ERR_INVALID_ARG; }
+  if (!(c->mg_omega >= 0 && c->mg_omega < 1)) { why = "mg_omega must be in [0, 1)"; return NI_ERR_INVALID_ARG; }
+  if (!(c->mg_correction >= 0 && c->mg_correction <= 3)) { why = "mg_correction must be in [0, 3]"; return NI_ERR_INVALID_ARG; }
+  if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;
 }
@@ -227,6 +235,7 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   dfree(h->blk); dfree(h->d_count); dfree(h->radix_hist); dfree(h->st);
   dfree(h->in_normals); dfree(h->in_mask); dfree(h->out_depth);
   dfree(h->tile_in); dfree(h->tile_out);
+  free_mg(h);
   if (h->net) ni_cnn_destroy(h->net);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (int i = 0; i < 8; ++i)

@@ -24,6 +24,7 @@
 #define NI_SPIN_LIMIT_CYCLES (4000000000LL)
 
 #define NI_MAX_T 256
+#define NI_MG_MAX_LEVELS 24   // multigrid levels of the fill (2^24 > any image side)
 
 // kernel-launch counter of a handle (graph replays add their captured count)
 #define NI_COUNT(h) ((h)->launches++)
@@ -140,6 +141,22 @@ struct ni_handle {
   int* csr_pair = nullptr;     // [2 * Ecap]
   int* radix_hist = nullptr;   // [256 * NI_SORT_BLOCKS]
 
+  // multigrid hierarchy of the fill (precond = 1): coarse levels 1..mg_L in pools
+  int mg_L = 0;
+  int mg_h[NI_MG_MAX_LEVELS + 1] = {}, mg_w[NI_MG_MAX_LEVELS + 1] = {};
+  long long mg_off[NI_MG_MAX_LEVELS + 1] = {};
+  long long mg_cells = 0;      // pool size (0: not allocated)
+  int* mg_lab = nullptr;
+  float* mg_wr = nullptr;
+  float* mg_wd = nullptr;
+  float* mg_d = nullptr;       // leak: diagonal minus the cell's edge weights
+  float* mg_invd = nullptr;
+  float* mg_b = nullptr;       // restricted residuals
+  float* mg_e = nullptr;       // coarse corrections
+  uint8_t* mg_inc = nullptr;   // cell aggregated into its parent
+  uint8_t* inc0 = nullptr;     // the same for the pixels
+  float* z = nullptr;          // preconditioned residual
+
   DevState* st = nullptr;      // device
   DevState* st_host = nullptr; // pinned mirror
 
@@ -172,6 +189,7 @@ struct ni_handle {
 // ----------------------------------------------------------------------------
 // launch geometry
 // ----------------------------------------------------------------------------
+#define NI_MG_MAX_LEVELS 24
 #define NI_TILE_PX 1024
 #define NI_TILE_W 32
 #define NI_TILE_H 32
@@ -195,6 +213,8 @@ void scan_blocks_launch(int* blk, int nblocks, int* total_out, cudaStream_t s);
 // ni_fill.cu
 ni_status fill_setup_launch(ni_handle* h, cudaStream_t s);
 ni_status fill_solve_launch(ni_handle* h, cudaStream_t s);
+ni_status mg_solve_launch(ni_handle* h, cudaStream_t s);
+void free_mg(ni_handle* h);
 void export_logdepth_launch(ni_handle* h, float* out, cudaStream_t s);
 void import_logdepth_launch(ni_handle* h, const float* in, cudaStream_t s);
 void output_depth_launch(ni_handle* h, float* depth, cudaStream_t s);

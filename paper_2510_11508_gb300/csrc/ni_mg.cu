@@ -1,0 +1,864 @@
+// Fill solve with a multigrid-preconditioned CG (row a4, precond = 1).
+//
+// The fill systems of Eq. 10 are weighted graph Laplacians of the pixel grid,
+// one block per component.  Jacobi-PCG needs a number of iterations that grows
+// with the component's diameter (thousands on the large maps).  Here the
+// preconditioner is one symmetric V-cycle of an aggregation multigrid built on
+// the grid itself:
+//
+//   * level l+1 aggregates 2x2 cells of level l.  The coarse cell takes the
+//     label of the first valid cell of its block (raster order); block cells of
+//     another label are not aggregated (zero row of the prolongation), so every
+//     coarse cell, and every coarse edge, stays inside one component and the
+//     preconditioner is block-diagonal per component like the system;
+//   * the coarse operator is the Galerkin product P^T A P of the piecewise-
+//     constant prolongation: a 5-point stencil again, with edge weights summed
+//     over the fine edges between two aggregates and the diagonal d_I = the
+//     weights of all edges leaving the aggregate plus its cells' own diagonal
+//     excess (sums of non-negative terms only);
+//   * smoothing: one damped Jacobi step (weight om) before and after the coarse
+//     correction, the coarse correction scaled by sc (over-correction of
+//     piecewise-constant aggregation); the coarsest level (<= 4 cells) takes a
+//     few Jacobi steps.  The cycle is a fixed symmetric positive definite
+//     operator, so CG with it converges like CG on a well-conditioned system.
+//
+// One cooperative persistent launch runs the whole solve.  Per iteration k:
+//   V-cycle on r_k (restriction of level 0 and the large levels by all CTAs,
+//   levels of at most `cta_cells` cells by CTA 0 alone), z_k and r_k^T z_k;
+//   phase A: p_k = z_k + beta_k p_{k-1}, q = A p_k, p^T A p per component;
+//   phase B: x += alpha p, r -= alpha q, r^T r per component.
+// Step lengths, convergence masks and iteration counts are per component, as
+// in the Jacobi kernel; level-0 passes walk the list of 32x32 tiles that hold
+// a valid pixel and skip tiles of converged components.
+#include <algorithm>
+
+#include "ni_internal.cuh"
+#include "ni_tile.cuh"
+
+struct MgArgs {
+  const float* wr;
+  const float* wd;
+  const float* invd;
+  const float* rhs;
+  const int* labels;
+  const int* tile_lab;
+  const uint8_t* inc0;     // level-0 cell aggregated into its level-1 cell
+  float* x;
+  float* r;
+  float* pb0;
+  float* pb1;
+  float* q;
+  float* z;
+  // coarse levels 1..L in pools; level l starts at loff[l]
+  int* clab;
+  float* cwr;
+  float* cwd;
+  float* cinvd;
+  float* cb;
+  float* ce;
+  const uint8_t* cinc;
+  int L, Lc;
+  int lh[NI_MG_MAX_LEVELS + 1], lw[NI_MG_MAX_LEVELS + 1];
+  long long loff[NI_MG_MAX_LEVELS + 1];
+  double* cs;
+  int* ci;
+  int2* tiles;             // list of tiles with a valid pixel (tile, uniform label)
+  int* ntl;                // [0] list length, [2..3] active counts by parity
+  DevState* st;
+  int N, H, W, K, Kc, ntiles, ntx, maxit, warm, ncs;
+  float om, sc;
+  double tol2;
+};
+
+// view of one coarse level
+struct Lv {
+  const int* lab;
+  const float* wr;
+  const float* wd;
+  const float* invd;
+  float* b;
+  float* e;
+  const uint8_t* inc;
+  int H, W;
+};
+
+__device__ __forceinline__ Lv coarse_level(const MgArgs& A, int l) {
+  Lv v;
+  const long long o = A.loff[l];
+  v.lab = A.clab + o; v.wr = A.cwr + o; v.wd = A.cwd + o; v.invd = A.cinvd + o;
+  v.b = A.cb + o; v.e = A.ce + o; v.inc = A.cinc + o;
+  v.H = A.lh[l]; v.W = A.lw[l];
+  return v;
+}
+
+// b_a - (A (om D^-1 b))_a at cell (y, x) of a level: the residual after one damped
+// Jacobi step from zero (difference form of the stencil)
+__device__ __forceinline__ float res_jac(const float* __restrict__ b, const float* __restrict__ invd,
+                                         const float* __restrict__ wr, const float* __restrict__ wd, int H,
+                                         int W, int y, int x, float om) {
+  const int a = y * W + x;
+  const float ya = om * invd[a] * b[a];
+  float s = 0.f;
+  const float w0 = wr[a];
+  if (w0 != 0.f) s += w0 * (ya - om * invd[a + 1] * b[a + 1]);
+  if (x > 0) {
+    const float w1 = wr[a - 1];
+    if (w1 != 0.f) s += w1 * (ya - om * invd[a - 1] * b[a - 1]);
+  }
+  const float w2 = wd[a];
+  if (w2 != 0.f) s += w2 * (ya - om * invd[a + W] * b[a + W]);
+  if (y > 0) {
+    const float w3 = wd[a - W];
+    if (w3 != 0.f) s += w3 * (ya - om * invd[a - W] * b[a - W]);
+  }
+  return b[a] - s;
+}
+
+// pre-smoothed value plus the scaled coarse correction at cell (y, x)
+__device__ __forceinline__ float zc_at(const float* __restrict__ b, const float* __restrict__ invd,
+                                       const uint8_t* __restrict__ inc, const float* __restrict__ ec, int W,
+                                       int Wc, int y, int x, float om, float sc) {
+  const int a = y * W + x;
+  float z = om * invd[a] * b[a];
+  if (inc[a]) z += sc * ec[(y >> 1) * Wc + (x >> 1)];
+  return z;
+}
+
+// restriction of level l (>= 1) to level l+1 over cells i0, i0 + stride, ...
+__device__ void mg_down(const MgArgs& A, int l, int i0, int stride, const int* act) {
+  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+  const int nc = c.H * c.W;
+  for (int I = i0; I < nc; I += stride) {
+    const int cy = I / c.W, cx = I - cy * c.W;
+    const int lc = c.lab[I];
+    float s = 0.f;
+    if (lc >= 0 && (act == nullptr || act[lc])) {
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int fy = 2 * cy + dy, fx = 2 * cx + dx;
+          if (fy < f.H && fx < f.W && f.inc[fy * f.W + fx])
+            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, A.om);
+        }
+    }
+    c.b[I] = s;
+  }
+}
+
+// prolongation and post-smoothing on level l (>= 1): e_l from b_l and e_{l+1}
+__device__ void mg_up(const MgArgs& A, int l, int i0, int stride) {
+  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+  const int n = f.H * f.W;
+  for (int a = i0; a < n; a += stride) {
+    if (f.lab[a] < 0) { f.e[a] = 0.f; continue; }
+    const int y = a / f.W, x = a - y * f.W;
+    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, A.om, A.sc);
+    float s = 0.f;
+    const float w0 = f.wr[a];
+    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, A.om, A.sc));
+    if (x > 0) {
+      const float w1 = f.wr[a - 1];
+      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, A.om, A.sc));
+    }
+    const float w2 = f.wd[a];
+    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, A.om, A.sc));
+    if (y > 0) {
+      const float w3 = f.wd[a - f.W];
+      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, A.om, A.sc));
+    }
+    f.e[a] = za + A.om * f.invd[a] * (f.b[a] - s);
+  }
+}
+
+// the levels of at most cta_cells cells, in one CTA: restriction down to level
+// L, damped Jacobi steps there, prolongation and smoothing back up to level Lc
+__device__ void mg_cta_levels(const MgArgs& A, const int* act) {
+  for (int l = A.Lc; l < A.L; ++l) {
+    mg_down(A, l, threadIdx.x, blockDim.x, act);
+    __syncthreads();
+  }
+  const Lv c = coarse_level(A, A.L);
+  if (threadIdx.x == 0) {
+    float e[4] = {0.f, 0.f, 0.f, 0.f}, en[4];
+    const int n = c.H * c.W;   // <= 4
+    for (int it = 0; it < A.ncs; ++it) {
+      for (int a = 0; a < n; ++a) {
+        if (c.lab[a] < 0) { en[a] = 0.f; continue; }
+        const int y = a / c.W, x = a - y * c.W;
+        float s = 0.f;
+        if (x + 1 < c.W) s += c.wr[a] * (e[a] - e[a + 1]);
+        if (x > 0) s += c.wr[a - 1] * (e[a] - e[a - 1]);
+        if (y + 1 < c.H) s += c.wd[a] * (e[a] - e[a + c.W]);
+        if (y > 0) s += c.wd[a - c.W] * (e[a] - e[a - c.W]);
+        en[a] = e[a] + A.om * c.invd[a] * (c.b[a] - s);
+      }
+      for (int a = 0; a < n; ++a) e[a] = en[a];
+    }
+    for (int a = 0; a < n; ++a) c.e[a] = e[a];
+  }
+  __syncthreads();
+  for (int l = A.L - 1; l >= A.Lc; --l) {
+    mg_up(A, l, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
+// active at iteration k (pure function of the state left by iteration k-1)
+__device__ __forceinline__ bool comp_now(const MgArgs& A, int c, int k) {
+  const double* rr = A.cs + (size_t)(3 + (k & 1)) * A.Kc;
+  const double* bb = A.cs + 5 * (size_t)A.Kc;
+  const int* act = A.ci;
+  const bool was = (k == 0) || act[(size_t)((k - 1) & 1) * A.Kc + c];
+  return was && k < A.maxit && bb[c] > 0.0 && rr[c] > A.tol2 * bb[c];
+}
+
+// level-0 restriction for the tile t: each of the 256 threads owns one level-1
+// cell of the tile (16 x 16 cells)
+template <bool CHECK>
+__device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k) {
+  const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
+  const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
+  const int H1 = A.lh[1], W1 = A.lw[1];
+  if (cy >= H1 || cx >= W1) return;
+  const int I = cy * W1 + cx;
+  const int lc = A.clab[A.loff[1] + I];
+  float s = 0.f;
+  if (lc >= 0 && (!CHECK || comp_now(A, lc, k))) {
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int fy = 2 * cy + dy, fx = 2 * cx + dx;
+        if (fy < A.H && fx < A.W && A.inc0[fy * A.W + fx])
+          s += res_jac(A.r, A.invd, A.wr, A.wd, A.H, A.W, fy, fx, A.om);
+      }
+  }
+  A.cb[A.loff[1] + I] = s;
+}
+
+template <bool ALIGNED>
+__device__ __forceinline__ uchar4 ldinc(const uint8_t* p, int a, int nval) {
+  if (ALIGNED && nval == 4) return *reinterpret_cast<const uchar4*>(p + a);
+  return make_uchar4(nval > 0 ? p[a] : 0, nval > 1 ? p[a + 1] : 0, nval > 2 ? p[a + 2] : 0, nval > 3 ? p[a + 3] : 0);
+}
+
+__device__ __forceinline__ uint8_t u4get(const uchar4& v, int j) {
+  return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
+}
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
+  __shared__ double sh[8 * 3 + 8];
+  __shared__ int s_key[TAB_SLOTS];
+  __shared__ double s_val[TAB_SLOTS * 3];
+  __shared__ int s_lab[TAB_SLOTS];
+  __shared__ float s_f[TAB_SLOTS * 4];
+  const int Kc = A.Kc, K = A.K, W = A.W, H = A.H, N = A.N;
+  double* rzs = A.cs;                       // [2]
+  double* pq = A.cs + 2 * (size_t)Kc;
+  double* rrs = A.cs + 3 * (size_t)Kc;      // [2]
+  double* bb = A.cs + 5 * (size_t)Kc;
+  double* sx = A.cs + 6 * (size_t)Kc;       // [2] sum x, count
+  double* xb = A.cs + 8 * (size_t)Kc;
+  double* xax = A.cs + 9 * (size_t)Kc;
+  double* alph = A.cs + 10 * (size_t)Kc;
+  int* act = A.ci;                          // [2]
+  int* iters = A.ci + 2 * (size_t)Kc;
+  int* err = &A.st->err;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
+  const int l8 = threadIdx.x & 7;
+  const float om = A.om, sc = A.sc;
+  const int W1 = A.lw[1];
+  const float* e1 = A.ce + A.loff[1];
+  if (threadIdx.x < TAB_SLOTS) {
+    s_key[threadIdx.x] = -1;
+    s_val[threadIdx.x * 3] = s_val[threadIdx.x * 3 + 1] = s_val[threadIdx.x * 3 + 2] = 0.0;
+  }
+  __syncthreads();
+
+  // ---- prologue: list of tiles with a valid pixel; r_0 = b - A x0; r^T r, b^T b
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int ul = A.tile_lab[t];
+    if (ul == -2) continue;
+    const G4 g = group_of(t, A.ntx, H, W);
+    int lab[4];
+    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval);
+    const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+    const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+    float xl = __shfl_up_sync(NI_FULL, x4.w, 1), xr = __shfl_down_sync(NI_FULL, x4.x, 1);
+    float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+    if (l8 == 0) {
+      xl = (g.nval > 0 && g.col > 0) ? A.x[g.a - 1] : 0.f;
+      wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
+    }
+    if (l8 == 7) xr = (g.nval == 4 && g.col + 4 < W) ? A.x[g.a + 4] : 0.f;
+    const bool up = g.row > 0, dn = g.row + 1 < H;
+    const float4 xu = up ? ldg<ALIGNED>(A.x, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+    const float4 wu4 = up ? ldg<ALIGNED>(A.wd, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+    const float4 xd = dn ? ldg<ALIGNED>(A.x, g.a + W, g.nval) : make_float4(0, 0, 0, 0);
+    float4 r4;
+    float pv[3][4];
+    bool on[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float xa = f4get(x4, j);
+      const float xR = j < 3 ? f4get(x4, j + 1) : xr, xL = j > 0 ? f4get(x4, j - 1) : xl;
+      const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+      const float ax = f4get(wr4, j) * (xa - xR) + f4get(wd4, j) * (xa - f4get(xd, j)) + wl * (xa - xL) +
+                       f4get(wu4, j) * (xa - f4get(xu, j));
+      on[j] = lab[j] >= 0;
+      float ra = f4get(b4, j) - ax;
+      if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+      f4set(r4, j, ra);
+      if (A.warm) {
+        pv[0][j] = on[j] ? xa * f4get(b4, j) : 0.f;
+        pv[1][j] = on[j] ? xa * ax : 0.f;
+      } else {
+        pv[0][j] = 0.f;
+        pv[1][j] = ra * ra;
+      }
+      pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
+    }
+    stg<ALIGNED>(A.r, g.a, g.nval, r4);
+    stg<ALIGNED>(A.pb1, g.a, g.nval, make_float4(0, 0, 0, 0));
+    double* const dst[3] = {A.warm ? xb : sx, A.warm ? xax : rrs, bb};
+    const int key = ul >= 0 ? ul : group_key(lab, on);
+    float v[3];
+    group_values<3>(key, lab, on, pv, dst, v);
+    tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    if (threadIdx.x == 0) {
+      const int pos = atomicAdd(&A.ntl[0], 1);
+      A.tiles[pos] = make_int2(t, ul);
+    }
+  }
+  if (!grid_barrier(&A.st->bar, err)) return;
+  const int nt = *(volatile int*)&A.ntl[0];
+  for (int c = gtid; c < K; c += gthr) sx[c] = 0.0;   // slot borrowed above when not warm
+  if (A.warm) {
+    // energy-optimal scale of the warm start per component (alpha = 0: cold start)
+    for (int c = gtid; c < K; c += gthr) {
+      const double al = (xax[c] > 0.0 && xb[c] > 0.0) ? xb[c] / xax[c] : 0.0;
+      alph[c] = al;
+      if (al == 0.0 && bb[c] > 0.0) atomicAdd(&A.st->warm_fallbacks, 1);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+      const int t = A.tiles[i].x, ul = A.tiles[i].y;
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      float pv[1][4];
+      bool on[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        on[j] = lab[j] >= 0;
+        const float al = on[j] ? (float)alph[lab[j]] : 0.f;
+        f4set(x4, j, al * f4get(x4, j));
+        float ra = (1.f - al) * f4get(b4, j) + al * f4get(r4, j);
+        if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+        f4set(r4, j, ra);
+        pv[0][j] = ra * ra;
+      }
+      stg<ALIGNED>(A.x, g.a, g.nval, x4);
+      stg<ALIGNED>(A.r, g.a, g.nval, r4);
+      double* const dst[1] = {rrs};
+      const int key = ul >= 0 ? ul : group_key(lab, on);
+      float v[1];
+      group_values<1>(key, lab, on, pv, dst, v);
+      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+  }
+
+  for (int k = 0;; ++k) {
+    const int P = k & 1, Q = P ^ 1;
+    double* rz = rzs + (size_t)P * Kc;
+    // ---- V-cycle, level-0 restriction; bookkeeping of iteration k
+    for (int c = gtid; c < K; c += gthr) {
+      const bool was = (k == 0) || act[(size_t)Q * Kc + c];
+      const bool conv = !(bb[c] > 0.0 && rrs[(size_t)P * Kc + c] > A.tol2 * bb[c]);
+      const bool nw = comp_now(A, c, k);
+      if (was && !conv && k >= A.maxit) {
+        atomicAdd(&A.st->fill_unconv, 1);
+        atomicOr(err, NI_DEV_ERR_FILL_NOCONV);
+      }
+      act[(size_t)P * Kc + c] = nw ? 1 : 0;
+      if (nw) {
+        iters[c] += 1;
+        atomicAdd(&A.ntl[2 + P], 1);
+      }
+      pq[c] = 0.0;
+    }
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+      const int t = A.tiles[i].x, ul = A.tiles[i].y;
+      if (ul >= 0) {
+        if (comp_now(A, ul, k)) down0_tile<false>(A, t, k);
+        else {
+          // the tile's level-1 cells belong to a converged component: zero them
+          const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
+          const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
+          if (cy < A.lh[1] && cx < W1) A.cb[A.loff[1] + cy * W1 + cx] = 0.f;
+        }
+      } else {
+        down0_tile<true>(A, t, k);
+      }
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+    if (*(volatile int*)&A.ntl[2 + P] == 0) break;
+    const int* actk = act + (size_t)P * Kc;
+    for (int l = 1; l < A.Lc; ++l) {
+      mg_down(A, l, gtid, gthr, actk);
+      if (!grid_barrier(&A.st->bar, err)) return;
+    }
+    if (blockIdx.x == 0) mg_cta_levels(A, actk);
+    if (!grid_barrier(&A.st->bar, err)) return;
+    for (int l = A.Lc - 1; l >= 1; --l) {
+      mg_up(A, l, gtid, gthr);
+      if (!grid_barrier(&A.st->bar, err)) return;
+    }
+    // ---- level-0 prolongation and smoothing: z_k; r^T z per component
+    if (gtid == 0) A.ntl[2 + Q] = 0;
+    for (int c = gtid; c < K; c += gthr) rrs[(size_t)Q * Kc + c] = 0.0;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+      const int t = A.tiles[i].x, ul = A.tiles[i].y;
+      if (ul >= 0 && !actk[ul]) continue;   // uniform across the CTA
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      if (ul >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+      } else {
+        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      }
+      bool now[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && actk[lab[j]];
+      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+      const uchar4 in4 = ldinc<ALIGNED>(A.inc0, g.a, g.nval);
+      // coarse corrections of the two level-1 cells under the thread's 4 pixels
+      float ec[4];
+      {
+        const int cy = g.row >> 1;
+        const float* er = e1 + (size_t)cy * W1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ec[j] = (j < g.nval && u4get(in4, j)) ? er[(g.col + j) >> 1] : 0.f;
+      }
+      float4 zc;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) f4set(zc, j, om * f4get(id4, j) * f4get(r4, j) + sc * ec[j]);
+      float zl = __shfl_up_sync(NI_FULL, zc.w, 1), zr = __shfl_down_sync(NI_FULL, zc.x, 1);
+      float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+      if (l8 == 0) {
+        wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
+        zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc) : 0.f;
+      }
+      if (l8 == 7)
+        zr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f)
+                 ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc)
+                 : 0.f;
+      float4 zu = make_float4(0, 0, 0, 0), zd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
+      if (g.row > 0) {
+        wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
+        const float4 ru = ldg<ALIGNED>(A.r, g.a - W, g.nval), iu = ldg<ALIGNED>(A.invd, g.a - W, g.nval);
+        const uchar4 cu = ldinc<ALIGNED>(A.inc0, g.a - W, g.nval);
+        const float* er = e1 + (size_t)((g.row - 1) >> 1) * W1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < g.nval && f4get(wu4, j) != 0.f)
+            f4set(zu, j, om * f4get(iu, j) * f4get(ru, j) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+      }
+      if (g.row + 1 < H) {
+        const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
+        const uchar4 cd = ldinc<ALIGNED>(A.inc0, g.a + W, g.nval);
+        const float* er = e1 + (size_t)((g.row + 1) >> 1) * W1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < g.nval && f4get(wd4, j) != 0.f)
+            f4set(zd, j, om * f4get(idd, j) * f4get(rd, j) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+      }
+      float4 z4;
+      float pv[1][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float za = f4get(zc, j);
+        const float zR = j < 3 ? f4get(zc, j + 1) : zr, zL = j > 0 ? f4get(zc, j - 1) : zl;
+        const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+        const float az = f4get(wr4, j) * (za - zR) + f4get(wd4, j) * (za - f4get(zd, j)) + wl * (za - zL) +
+                         f4get(wu4, j) * (za - f4get(zu, j));
+        const float zf = now[j] ? za + om * f4get(id4, j) * (f4get(r4, j) - az) : 0.f;
+        f4set(z4, j, zf);
+        pv[0][j] = zf * f4get(r4, j);
+      }
+      stg<ALIGNED>(A.z, g.a, g.nval, z4);
+      double* const dst[1] = {rz};
+      const int key = ul >= 0 ? ul : group_key(lab, now);
+      float v[1];
+      group_values<1>(key, lab, now, pv, dst, v);
+      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+
+    // ---- phase A: p_k = z_k + beta_k p_{k-1}; q = A p_k; p^T A p per component
+    const float* pold = Q ? A.pb1 : A.pb0;
+    float* pnew = P ? A.pb1 : A.pb0;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+      const int t = A.tiles[i].x, ul = A.tiles[i].y;
+      if (ul >= 0 && !actk[ul]) continue;
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      if (ul >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+      } else {
+        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      }
+      auto betaf = [&](int c) -> float {
+        const double ro = rzs[(size_t)Q * Kc + c];
+        return (k > 0 && ro > 0.0) ? (float)(rz[c] / ro) : 0.f;
+      };
+      const float4 z4 = ldg<ALIGNED>(A.z, g.a, g.nval), po4 = ldg<ALIGNED>(pold, g.a, g.nval);
+      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+      int sl[4];
+      tile_slots(ul, lab, sl, s_lab);
+      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) s_f[threadIdx.x * 4] = betaf(s_lab[threadIdx.x]);
+      __syncthreads();
+      float beta[4];
+      bool now[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        now[j] = lab[j] >= 0 && actk[lab[j]];
+        beta[j] = sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? betaf(lab[j]) : 0.f);
+      }
+      float4 pn;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) f4set(pn, j, now[j] ? f4get(z4, j) + beta[j] * f4get(po4, j) : 0.f);
+      float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
+      float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+      if (l8 == 0) {
+        const int a = g.a - 1;
+        wl0 = (g.nval > 0 && g.col > 0) ? A.wr[a] : 0.f;
+        pl = (wl0 != 0.f && now[0]) ? A.z[a] + beta[0] * pold[a] : 0.f;
+      }
+      if (l8 == 7) {
+        const int a = g.a + 4;
+        pr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f && now[3]) ? A.z[a] + beta[3] * pold[a] : 0.f;
+      }
+      float4 pu = make_float4(0, 0, 0, 0), pd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
+      if (g.row > 0) {
+        wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
+        const float4 zu = ldg<ALIGNED>(A.z, g.a - W, g.nval), pu0 = ldg<ALIGNED>(pold, g.a - W, g.nval);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          f4set(pu, j, (now[j] && f4get(wu4, j) != 0.f) ? f4get(zu, j) + beta[j] * f4get(pu0, j) : 0.f);
+      }
+      if (g.row + 1 < H) {
+        const float4 zd = ldg<ALIGNED>(A.z, g.a + W, g.nval), pd0 = ldg<ALIGNED>(pold, g.a + W, g.nval);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          f4set(pd, j, (now[j] && f4get(wd4, j) != 0.f) ? f4get(zd, j) + beta[j] * f4get(pd0, j) : 0.f);
+      }
+      float4 q4;
+      float pv[1][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float pa = f4get(pn, j);
+        const float pR = j < 3 ? f4get(pn, j + 1) : pr, pL = j > 0 ? f4get(pn, j - 1) : pl;
+        const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+        const float dR = pa - pR, dD = pa - f4get(pd, j);
+        const float qa = f4get(wr4, j) * dR + f4get(wd4, j) * dD + wl * (pa - pL) + f4get(wu4, j) * (pa - f4get(pu, j));
+        f4set(q4, j, now[j] ? qa : 0.f);
+        pv[0][j] = now[j] ? f4get(wr4, j) * dR * dR + f4get(wd4, j) * dD * dD : 0.f;
+      }
+      stg<ALIGNED>(pnew, g.a, g.nval, pn);
+      stg<ALIGNED>(A.q, g.a, g.nval, q4);
+      double* const dst[1] = {pq};
+      const int key = ul >= 0 ? ul : group_key(lab, now);
+      float v[1];
+      group_values<1>(key, lab, now, pv, dst, v);
+      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+
+    // ---- phase B: alpha_k; x += alpha p; r -= alpha q; r^T r per component
+    for (int c = gtid; c < K; c += gthr) rzs[(size_t)Q * Kc + c] = 0.0;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+      const int t = A.tiles[i].x, ul = A.tiles[i].y;
+      if (ul >= 0 && !actk[ul]) continue;
+      const G4 g = group_of(t, A.ntx, H, W);
+      int lab[4];
+      if (ul >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+      } else {
+        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+      }
+      auto alphaf = [&](int c) -> float {
+        const double pp = pq[c];
+        return pp > 0.0 ? (float)(rz[c] / pp) : 0.f;
+      };
+      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 p4 = ldg<ALIGNED>(pnew, g.a, g.nval), q4 = ldg<ALIGNED>(A.q, g.a, g.nval);
+      int sl[4];
+      tile_slots(ul, lab, sl, s_lab);
+      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) s_f[threadIdx.x * 4] = alphaf(s_lab[threadIdx.x]);
+      __syncthreads();
+      float pv[1][4];
+      bool now[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        now[j] = lab[j] >= 0 && actk[lab[j]];
+        const float al = !now[j] ? 0.f : (sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? alphaf(lab[j]) : 0.f));
+        f4set(x4, j, f4get(x4, j) + al * f4get(p4, j));
+        const float ra = f4get(r4, j) - al * f4get(q4, j);
+        f4set(r4, j, ra);
+        pv[0][j] = now[j] ? ra * ra : 0.f;
+      }
+      stg<ALIGNED>(A.x, g.a, g.nval, x4);
+      stg<ALIGNED>(A.r, g.a, g.nval, r4);
+      double* const dst[1] = {rrs + (size_t)Q * Kc};
+      const int key = ul >= 0 ? ul : group_key(lab, now);
+      float v[1];
+      group_values<1>(key, lab, now, pv, dst, v);
+      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    }
+    if (!grid_barrier(&A.st->bar, err)) return;
+  }
+  // ---- epilogue: zero mean per component, statistics
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+    const int t = A.tiles[i].x, ul = A.tiles[i].y;
+    const G4 g = group_of(t, A.ntx, H, W);
+    int lab[4];
+    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
+    float pv[2][4];
+    bool on[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      on[j] = lab[j] >= 0;
+      pv[0][j] = on[j] ? f4get(x4, j) : 0.f;
+      pv[1][j] = on[j] ? 1.f : 0.f;
+    }
+    double* const dst[2] = {sx, sx + Kc};
+    const int key = ul >= 0 ? ul : group_key(lab, on);
+    float v[2];
+    group_values<2>(key, lab, on, pv, dst, v);
+    tile_accum<true, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+  }
+  if (!grid_barrier(&A.st->bar, err)) return;
+  for (int a = gtid; a < N; a += gthr) {
+    const int c = A.labels[a];
+    if (c >= 0) {
+      const double cnt = sx[(size_t)Kc + c];
+      if (cnt > 0) A.x[a] = (float)((double)A.x[a] - sx[c] / cnt);
+    }
+  }
+  for (int c = gtid; c < K; c += gthr) {
+    atomicMax(&A.st->fill_iters, iters[c]);
+    if (iters[c] > 0)
+      atomicAdd(&A.st->fill_px_iters, (unsigned long long)iters[c] * (unsigned long long)sx[(size_t)Kc + c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// hierarchy setup: level l+1 from level l (Galerkin product of the 2x2
+// piecewise-constant aggregation restricted to same-label cells)
+// ---------------------------------------------------------------------------
+struct LvIn {
+  const int* lab;
+  const float* wr;
+  const float* wd;
+  const float* s;      // leak of each cell (diagonal minus its edge weights); nullptr: 0 (level 0)
+  uint8_t* inc;        // written: cell aggregated into its parent
+  int H, W;
+};
+
+__device__ __forceinline__ int first_label(const LvIn& f, int cy, int cx) {
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int y = 2 * cy + dy, x = 2 * cx + dx;
+      if (y < f.H && x < f.W) {
+        const int l = f.lab[y * f.W + x];
+        if (l >= 0) return l;
+      }
+    }
+  return -1;
+}
+
+// Every sum is over non-negative terms (no cancellation): the diagonal of an
+// aggregate is its cells' leaks plus the weights of all edges that leave the
+// block; its leak is the part of that which no coarse edge carries (leaks of
+// its cells and edges to cells that are not aggregated into their own parent).
+__global__ void k_mg_coarsen(LvIn f, int Hc, int Wc, int* __restrict__ clab, float* __restrict__ cwr,
+                             float* __restrict__ cwd, float* __restrict__ cs, float* __restrict__ cinvd) {
+  const int nc = Hc * Wc;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    const int cy = I / Wc, cx = I - cy * Wc;
+    const int lc = first_label(f, cy, cx);
+    float wrc = 0.f, wdc = 0.f, dc = 0.f, sc = 0.f;
+    const int flR = (lc >= 0 && cx + 1 < Wc) ? first_label(f, cy, cx + 1) : -1;
+    const int flL = (lc >= 0 && cx > 0) ? first_label(f, cy, cx - 1) : -1;
+    const int flD = (lc >= 0 && cy + 1 < Hc) ? first_label(f, cy + 1, cx) : -1;
+    const int flU = (lc >= 0 && cy > 0) ? first_label(f, cy - 1, cx) : -1;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int y = 2 * cy + dy, x = 2 * cx + dx;
+        if (y >= f.H || x >= f.W) continue;
+        const int a = y * f.W + x;
+        const bool in = lc >= 0 && f.lab[a] == lc;
+        f.inc[a] = in ? 1 : 0;
+        if (!in) continue;
+        const float sa = f.s ? f.s[a] : 0.f;
+        dc += sa;
+        sc += sa;
+        if (dx == 1) {                      // edge to the block on the right
+          const float w = f.wr[a];
+          dc += w;
+          if (flR == lc) wrc += w; else sc += w;
+        } else if (x > 0) {                 // edge to the block on the left
+          const float w = f.wr[a - 1];
+          dc += w;
+          if (flL != lc) sc += w;
+        }
+        if (dy == 1) {                      // edge to the block below
+          const float w = f.wd[a];
+          dc += w;
+          if (flD == lc) wdc += w; else sc += w;
+        } else if (y > 0) {                 // edge to the block above
+          const float w = f.wd[a - f.W];
+          dc += w;
+          if (flU != lc) sc += w;
+        }
+      }
+    clab[I] = lc;
+    cwr[I] = wrc;
+    cwd[I] = wdc;
+    cs[I] = sc;
+    cinvd[I] = dc > 0.f ? 1.0f / dc : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int grid_cells(ni_handle* h, long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::max(1LL, std::min(b, (long long)h->num_sms * 8));
+}
+
+static ni_status ensure_mg(ni_handle* h, cudaStream_t s) {
+  if (h->mg_cells > 0) return NI_OK;
+  // level dimensions: halve until a level holds at most 4 cells
+  long long total = 0;
+  int L = 0, hh = h->H, ww = h->W;
+  h->mg_h[0] = hh; h->mg_w[0] = ww; h->mg_off[0] = 0;
+  do {
+    hh = (hh + 1) / 2; ww = (ww + 1) / 2;
+    ++L;
+    if (L > NI_MG_MAX_LEVELS) return ni_fail(h, NI_ERR_INVALID_ARG, "multigrid: too many levels");
+    h->mg_h[L] = hh; h->mg_w[L] = ww;
+    h->mg_off[L] = total;
+    total += ((long long)hh * ww + 63) / 64 * 64;
+  } while ((long long)hh * ww > 4);
+  h->mg_L = L;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](auto** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, n * sizeof(**p));
+  };
+  al(&h->mg_lab, total); al(&h->mg_wr, total); al(&h->mg_wd, total); al(&h->mg_d, total);
+  al(&h->mg_invd, total); al(&h->mg_b, total); al(&h->mg_e, total); al(&h->mg_inc, total);
+  al(&h->inc0, (size_t)h->Npad); al(&h->z, (size_t)h->Npad);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ni_fail(h, NI_ERR_OOM, "multigrid hierarchy allocation failed");
+  }
+  h->mg_cells = total;
+  cudaMemsetAsync(h->mg_b, 0, total * sizeof(float), s);
+  cudaMemsetAsync(h->mg_e, 0, total * sizeof(float), s);
+  cudaMemsetAsync(h->mg_inc, 0, total, s);
+  cudaMemsetAsync(h->inc0, 0, (size_t)h->Npad, s);
+  cudaMemsetAsync(h->z, 0, sizeof(float) * (size_t)h->Npad, s);
+  return ni_cuda_check(h, cudaGetLastError(), "multigrid allocation");
+}
+
+void free_mg(ni_handle* h) {
+  cudaFree(h->mg_lab); cudaFree(h->mg_wr); cudaFree(h->mg_wd); cudaFree(h->mg_d); cudaFree(h->mg_invd);
+  cudaFree(h->mg_b); cudaFree(h->mg_e); cudaFree(h->mg_inc); cudaFree(h->inc0); cudaFree(h->z);
+  h->mg_lab = nullptr; h->mg_wr = h->mg_wd = h->mg_d = h->mg_invd = h->mg_b = h->mg_e = nullptr;
+  h->mg_inc = h->inc0 = nullptr; h->z = nullptr;
+  h->mg_cells = 0;
+}
+
+ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
+  ni_status rc = ensure_mg(h, s);
+  if (rc != NI_OK) return rc;
+  const int L = h->mg_L;
+  // hierarchy for the current weights
+  for (int l = 0; l < L; ++l) {
+    LvIn f;
+    if (l == 0) {
+      f.lab = h->labels; f.wr = h->wr; f.wd = h->wd; f.s = nullptr; f.inc = h->inc0;
+    } else {
+      const long long o = h->mg_off[l];
+      f.lab = h->mg_lab + o; f.wr = h->mg_wr + o; f.wd = h->mg_wd + o; f.s = h->mg_d + o; f.inc = h->mg_inc + o;
+    }
+    f.H = h->mg_h[l]; f.W = h->mg_w[l];
+    const long long oc = h->mg_off[l + 1];
+    const int Hc = h->mg_h[l + 1], Wc = h->mg_w[l + 1];
+    k_mg_coarsen<<<grid_cells(h, (long long)Hc * Wc), 256, 0, s>>>(f, Hc, Wc, h->mg_lab + oc, h->mg_wr + oc,
+                                                                   h->mg_wd + oc, h->mg_d + oc, h->mg_invd + oc);
+    NI_COUNT(h);
+  }
+  const bool f64 = h->cfg.precision == 0;
+  const bool aligned = (h->W % 4) == 0;
+  void* fn = f64 ? (aligned ? (void*)k_pcg_mg<true, true> : (void*)k_pcg_mg<true, false>)
+                 : (aligned ? (void*)k_pcg_mg<false, true> : (void*)k_pcg_mg<false, false>);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NI_TILE_THREADS, 0);
+  if (per_sm < 1) return ni_fail(h, NI_ERR_CUDA, "multigrid PCG: kernel cannot be resident");
+  const int want = h->cfg.tile_w > 0 ? h->cfg.tile_w : 4;
+  int grid = h->num_sms * std::min(per_sm, want);
+  grid = std::max(1, std::min(grid, h->ntiles));
+  cudaMemsetAsync(h->cacc, 0, sizeof(double) * 14 * (size_t)h->Kcap, s);
+  cudaMemsetAsync(h->cflag, 0, sizeof(int) * 3 * (size_t)h->Kcap, s);
+  cudaMemsetAsync(&h->st->bar, 0, sizeof(GridBar), s);
+  int* ntl = h->blk;   // scan scratch is free during the fill: [0] tiles, [2..3] active counts
+  cudaMemsetAsync(ntl, 0, 4 * sizeof(int), s);
+  MgArgs a;
+  a.wr = h->wr; a.wd = h->wd; a.invd = h->invd; a.rhs = h->b; a.labels = h->labels; a.tile_lab = h->tile_lab;
+  a.inc0 = h->inc0;
+  a.x = h->x; a.r = h->r; a.pb0 = h->p; a.pb1 = h->p2; a.q = h->q; a.z = h->z;
+  a.clab = h->mg_lab; a.cwr = h->mg_wr; a.cwd = h->mg_wd; a.cinvd = h->mg_invd; a.cb = h->mg_b; a.ce = h->mg_e;
+  a.cinc = h->mg_inc;
+  a.L = L;
+  // first level small enough for one CTA
+  int Lc = L;
+  const long long cta_cells = h->cfg.mg_cta_cells > 0 ? h->cfg.mg_cta_cells : 4096;
+  for (int l = 1; l <= L; ++l)
+    if ((long long)h->mg_h[l] * h->mg_w[l] <= cta_cells) { Lc = l; break; }
+  a.Lc = Lc;
+  for (int l = 0; l <= NI_MG_MAX_LEVELS; ++l) {
+    a.lh[l] = l <= L ? h->mg_h[l] : 0;
+    a.lw[l] = l <= L ? h->mg_w[l] : 0;
+    a.loff[l] = l <= L ? h->mg_off[l] : 0;
+  }
+  a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
+  a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
+  a.maxit = h->cfg.cg_maxit; a.warm = h->cfg.warm_start ? 1 : 0;
+  a.ncs = 4;
+  a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.67f;
+  a.sc = h->cfg.mg_correction > 0 ? (float)h->cfg.mg_correction : 1.5f;
+  a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
+  void* args[] = {&a};
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);
+  NI_COUNT(h);
+  return ni_cuda_check(h, e, "multigrid PCG launch");
+}

@@ -23,8 +23,9 @@ def _run(name, **over):
 
 
 @pytest.mark.parametrize("name", ["c1", "c2", "c3_small"])
-def test_integrate_matches_oracle(name):
-    w, depth, labels, st, ref = _run(name)
+@pytest.mark.parametrize("precond", [0, 1])
+def test_integrate_matches_oracle(name, precond):
+    w, depth, labels, st, ref = _run(name, precond=precond)
     zg = np.log(depth) if w.camera["camera"] == 1 else depth
     zr = np.nan_to_num(ref["z"])
     err = rel_depth_error(np.nan_to_num(zg), zr, w.mask, w.camera["camera"])
@@ -54,9 +55,24 @@ def test_integrate_host_equals_device():
     assert np.nanmax(np.abs(a - b) / np.abs(b)) < 1e-5
 
 
-def test_full_size_c3():
-    w, depth, labels, st, ref = _run("c3")
-    zg = np.log(depth)
-    err = rel_depth_error(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, 1)
-    print("c3", st, "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
+_C3_REF = {}
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_full_size_c3(precond):
+    w = make_workload("c3")
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params, precond=precond)
+    depth, labels, st = it.integrate(n, m)
+    if "ref" not in _C3_REF:
+        _C3_REF["ref"] = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(w.params))
+    ref = _C3_REF["ref"]
+    depth, labels = depth.cpu().numpy(), labels.cpu().numpy()
+    err = rel_depth_error(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
+    print("c3 precond", precond, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "ms_fill", "ms_total")},
+          "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
     assert st["K0"] == ref["K0"]
+    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
+    np.testing.assert_array_equal(labels, ref["labels"])
+    assert err <= 1e-4

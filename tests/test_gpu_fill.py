@@ -71,3 +71,55 @@ def test_fill_irls_sweeps():
     z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1)
     d = (z - zr)[w.mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
+
+
+# ---- multigrid-preconditioned batched fill (precond = 1): same answer, fewer iterations
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3_small"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fill_multigrid_matches_oracle(name, precision):
+    w = make_workload(name)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=1, precond=1, precision=precision)
+    m = w.mask > 0
+    d = (z - zr)[m]
+    scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[m]))
+    rms = float(np.sqrt(np.mean(d * d))) / scale
+    print(f"{name} multigrid prec={precision} K={K} fill rms={rms:.3e} max={np.abs(d).max():.3e}")
+    assert rms <= TOL[precision]
+
+
+def test_fill_multigrid_exact_plane():
+    nrm, mask, z, cam = G.plane_map(40, 53, G.PERSP, normal=(0.3, -0.2, -1.0), d=30.0, dtype=np.float32)
+    zf, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 5.0}, batched=1, precond=1)
+    assert K == 1
+    rms, mx = island_rms(zf, np.log(z), mask)
+    assert rms < 2e-6, rms
+
+
+@pytest.mark.parametrize("H,W", [(45, 77), (1, 93), (97, 1), (2, 2), (33, 65)])
+def test_fill_multigrid_ragged_shapes(H, W):
+    nrm, mask, cam = G.random_normal_field(H, W, n_dirs=2, jitter_deg=0.8, hole_frac=0.05, seed=H * W,
+                                           block=9)
+    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=1)
+    d = (z - zr)[mask > 0]
+    assert np.sqrt(np.mean(d * d)) < 1e-4 if d.size else True
+
+
+def test_fill_multigrid_irls_sweeps():
+    w = make_workload("c3_small")
+    p = dict(w.params, n_fill_irls=2)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1, precond=1)
+    d = (z - zr)[w.mask > 0]
+    assert np.sqrt(np.mean(d * d)) < 1e-4
+
+
+def test_multigrid_needs_fewer_iterations():
+    w = make_workload("c3_small")
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    its = {}
+    for pc in (0, 1):
+        it = integrator(H, W, w.camera, w.params, batched=1, precond=pc)
+        its[pc] = it.integrate(n, m)[2]["fill_iters"]
+    print("fill iterations jacobi / multigrid", its)
+    assert its[1] * 4 < its[0]
