@@ -27,10 +27,18 @@ sys.path.insert(0, ROOT)
 METRIC = ("valid Mpixel/s integrated at ≤1e-3 rel depth RMSE vs FP64 oracle; "
           "stencil GB/s vs HBM peak")
 UNIT = "Mpixel/s"
-# algorithmic bytes of one batched-PCG iteration per active pixel: read p, x, r
-# (4 B each), the right/down weights (8 B), the inverse diagonal (4 B) and the
-# component label (4 B); write p, x, r (4 B each)
+# Algorithmic bytes per active pixel and iteration of the fill kernels.
+# Jacobi (k_pcg_tiles): read p, x, r (4 B each), the right/down weights (8 B),
+# the inverse diagonal (4 B) and the label (4 B); write p, x, r (4 B each).
 PCG_BYTES_PER_PX_ITER = 40
+# Multigrid (k_pcg_mg), level 0 in four passes: restriction reads r, 1/d,
+# w right/down (16 B) and the aggregation flag (1 B) and writes a quarter of a
+# float (1 B); prolongation + smoothing reads the same 17 B plus a quarter of the
+# coarse correction (1 B) and writes z (4 B); the direction pass reads z, p,
+# w right/down (16 B) and writes p, q (8 B); the update pass reads x, r, p, q
+# (16 B) and writes x, r (8 B): 88 B.  Levels 1.. hold a third of the cells
+# and move about 48 B per cell and iteration: 16 B per fine pixel.
+MG_BYTES_PER_PX_ITER = 104
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -43,6 +51,7 @@ def parse():
     ap.add_argument("--config", default="c3")
     ap.add_argument("--variant", default="batched", choices=["batched", "plain"])
     ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precond", type=int, default=1, help="batched fill: 0 Jacobi, 1 multigrid")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
     return ap.parse_args()
 
@@ -126,12 +135,13 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_per_px_iter():
-    """DRAM bytes per active pixel-iteration of the batched PCG kernel from the
-    committed ncu summary, if it was taken on the current kernel source."""
+def traffic_per_px_iter(kernel, source):
+    """DRAM bytes per active pixel-iteration of a fill kernel from the committed
+    ncu summary profiles/<kernel>_traffic.json, if it was taken on the current
+    kernel source."""
     import hashlib
-    p = os.path.join(ROOT, "profiles", "pcg_batched_traffic.json")
-    src = os.path.join(ROOT, "paper_2510_11508_gb300", "csrc", "ni_fill.cu")
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
+    src = os.path.join(ROOT, "paper_2510_11508_gb300", "csrc", source)
     try:
         d = json.load(open(p))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -161,7 +171,7 @@ def run_ours(args):
     H, W = w.mask.shape
     params = dict(w.params)
     cfg = ni.config_for(H, W, w.camera, params, batched=1 if args.variant == "batched" else 0,
-                        precision=args.precision)
+                        precision=args.precision, precond=args.precond)
     it = ni.Integrator(cfg)
     n = torch.from_numpy(w.normals).cuda()
     m = torch.from_numpy(w.mask).cuda()
@@ -246,21 +256,29 @@ def run_ours(args):
 
     peak, peak_src = peaks()
     per_launch_ms = fill_ms / args.steps
-    per_launch_bytes = PCG_BYTES_PER_PX_ITER * px_iters / args.steps
+    if args.variant == "batched" and args.precond == 1:
+        kernel, source, bpp = "k_pcg_mg", "ni_mg.cu", MG_BYTES_PER_PX_ITER
+    elif args.variant == "batched":
+        kernel, source, bpp = "k_pcg_tiles", "ni_fill.cu", PCG_BYTES_PER_PX_ITER
+    else:
+        kernel, source, bpp = "k_cg_spmv+k_cg_update+k_cg_dir", "ni_fill.cu", PCG_BYTES_PER_PX_ITER
+    per_launch_bytes = bpp * px_iters / args.steps
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
-    tpi = traffic_per_px_iter()
-    roof = {"kernel": "k_pcg_batched" if args.variant == "batched" else "plain PCG (k_cg_*)",
+    tpi = traffic_per_px_iter(kernel, source)
+    roof = {"kernel": kernel,
             "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": (tpi * px_iters / args.steps) if tpi is not None else None,
             "algorithmic_bytes_per_launch": per_launch_bytes,
-            "bytes_per_px_iter": PCG_BYTES_PER_PX_ITER,
+            "bytes_per_px_iter": bpp,
             "px_iters_per_launch": px_iters / args.steps, "ms_per_launch": per_launch_ms}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "description": w.description, "H": H, "W": W,
                        "n_valid": n_valid, "variant": args.variant,
+                       "fill_preconditioner": ("multigrid V-cycle" if args.precond == 1 else "Jacobi")
+                       if args.variant == "batched" else "Jacobi",
                        "reductions": "fp64" if args.precision == 0 else "fp32 tree + fp64 across CTAs",
                        "theta_c_deg": params["theta_c_deg"], "T": params["T"],
                        "can_merge": params["can_merge"], "freq_merging": params["freq_merging"],

@@ -92,12 +92,15 @@ typedef struct {
                                component by its energy-optimal factor; needs batched = 1 */
   int hard_outliers;        /* 1: hard W^out variant (supplementary, outlier ablation) */
   int validate;             /* 1: check normals (unit length within 1e-3, n.tau != 0) */
-  int tile_w, tile_h;       /* stencil tile shape (0 = tuned default) */
-  int precond;              /* preconditioner of the batched fill: 0 Jacobi, 1 one symmetric
-                               V-cycle of aggregation multigrid on the pixel grid */
-  double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.67) */
-  double mg_correction;     /* scale of the coarse-grid correction (0: 1.5) */
+  int ctas_per_sm;          /* CTAs per SM of the persistent fill kernels (0: 4) */
+  int mg_coarse_sweeps;     /* damped-Jacobi steps on the coarsest multigrid level (0: 4) */
+  int precond;              /* preconditioner of the batched fill: 0 Jacobi, 1 (default) one
+                               symmetric V-cycle of aggregation multigrid on the pixel grid */
+  double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.8) */
+  double mg_correction;     /* scale of the coarse-grid correction (0: 1) */
   int mg_cta_cells;         /* levels of at most this many cells run in one CTA (0: 4096) */
+  int mg_flags;             /* bit 0: project each component's mean out of the residual
+                               before the V-cycle */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

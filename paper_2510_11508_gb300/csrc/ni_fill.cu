@@ -856,7 +856,7 @@ static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NI_TILE_THREADS, 0);
   if (per_sm < 1) return ni_fail(h, NI_ERR_CUDA, "batched PCG: kernel cannot be resident");
-  const int want = h->cfg.tile_w > 0 ? h->cfg.tile_w : 4;   // CTAs per SM (tuned)
+  const int want = h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm : 4;   // CTAs per SM (tuned)
   int grid = h->num_sms * std::min(per_sm, want);
   grid = std::max(1, std::min(grid, h->ntiles));
   cudaMemsetAsync(h->cacc, 0, sizeof(double) * 14 * (size_t)h->Kcap, s);

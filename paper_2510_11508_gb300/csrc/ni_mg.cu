@@ -16,14 +16,15 @@
 //     over the fine edges between two aggregates and the diagonal d_I = the
 //     weights of all edges leaving the aggregate plus its cells' own diagonal
 //     excess (sums of non-negative terms only);
-//   * smoothing: one damped Jacobi step (weight om) before and after the coarse
-//     correction, the coarse correction scaled by sc (over-correction of
-//     piecewise-constant aggregation); the coarsest level (<= 4 cells) takes a
-//     few Jacobi steps.  The cycle is a fixed symmetric positive definite
+//   * smoothing: one damped Jacobi step (weight om, default 0.8) before and
+//     after the coarse correction, the coarse correction scaled by sc (default
+//     1; over-correction sc > 1 cut the iterations on some maps but left single
+//     components converging at a crawl in float32 on others); the coarsest level
+//     (<= 4 cells) takes a few Jacobi steps.  The cycle is a fixed symmetric positive definite
 //     operator, so CG with it converges like CG on a well-conditioned system.
 //
 // One cooperative persistent launch runs the whole solve.  Per iteration k:
-//   V-cycle on r_k (restriction of level 0 and the large levels by all CTAs,
+//   V-cycle on r_k minus its component mean (restriction of level 0 and the large levels by all CTAs,
 //   levels of at most `cta_cells` cells by CTA 0 alone), z_k and r_k^T z_k;
 //   phase A: p_k = z_k + beta_k p_{k-1}, q = A p_k, p^T A p per component;
 //   phase B: x += alpha p, r -= alpha q, r^T r per component.
@@ -65,7 +66,7 @@ struct MgArgs {
   int2* tiles;             // list of tiles with a valid pixel (tile, uniform label)
   int* ntl;                // [0] list length, [2..3] active counts by parity
   DevState* st;
-  int N, H, W, K, Kc, ntiles, ntx, maxit, warm, ncs;
+  int N, H, W, K, Kc, ntiles, ntx, maxit, warm, ncs, project;
   float om, sc;
   double tol2;
 };
@@ -91,35 +92,37 @@ __device__ __forceinline__ Lv coarse_level(const MgArgs& A, int l) {
   return v;
 }
 
-// b_a - (A (om D^-1 b))_a at cell (y, x) of a level: the residual after one damped
-// Jacobi step from zero (difference form of the stencil)
+// (b_a - mu) - (A (om D^-1 (b - mu)))_a at cell (y, x) of a level: the residual
+// after one damped Jacobi step from zero (difference form of the stencil; mu is
+// the component's mean of b, projected out at level 0, 0 on coarse levels)
 __device__ __forceinline__ float res_jac(const float* __restrict__ b, const float* __restrict__ invd,
                                          const float* __restrict__ wr, const float* __restrict__ wd, int H,
-                                         int W, int y, int x, float om) {
+                                         int W, int y, int x, float om, float mu) {
   const int a = y * W + x;
-  const float ya = om * invd[a] * b[a];
+  const float ba = b[a] - mu;
+  const float ya = om * invd[a] * ba;
   float s = 0.f;
   const float w0 = wr[a];
-  if (w0 != 0.f) s += w0 * (ya - om * invd[a + 1] * b[a + 1]);
+  if (w0 != 0.f) s += w0 * (ya - om * invd[a + 1] * (b[a + 1] - mu));
   if (x > 0) {
     const float w1 = wr[a - 1];
-    if (w1 != 0.f) s += w1 * (ya - om * invd[a - 1] * b[a - 1]);
+    if (w1 != 0.f) s += w1 * (ya - om * invd[a - 1] * (b[a - 1] - mu));
   }
   const float w2 = wd[a];
-  if (w2 != 0.f) s += w2 * (ya - om * invd[a + W] * b[a + W]);
+  if (w2 != 0.f) s += w2 * (ya - om * invd[a + W] * (b[a + W] - mu));
   if (y > 0) {
     const float w3 = wd[a - W];
-    if (w3 != 0.f) s += w3 * (ya - om * invd[a - W] * b[a - W]);
+    if (w3 != 0.f) s += w3 * (ya - om * invd[a - W] * (b[a - W] - mu));
   }
-  return b[a] - s;
+  return ba - s;
 }
 
 // pre-smoothed value plus the scaled coarse correction at cell (y, x)
 __device__ __forceinline__ float zc_at(const float* __restrict__ b, const float* __restrict__ invd,
                                        const uint8_t* __restrict__ inc, const float* __restrict__ ec, int W,
-                                       int Wc, int y, int x, float om, float sc) {
+                                       int Wc, int y, int x, float om, float sc, float mu) {
   const int a = y * W + x;
-  float z = om * invd[a] * b[a];
+  float z = om * invd[a] * (b[a] - mu);
   if (inc[a]) z += sc * ec[(y >> 1) * Wc + (x >> 1)];
   return z;
 }
@@ -139,7 +142,7 @@ __device__ void mg_down(const MgArgs& A, int l, int i0, int stride, const int* a
         for (int dx = 0; dx < 2; ++dx) {
           const int fy = 2 * cy + dy, fx = 2 * cx + dx;
           if (fy < f.H && fx < f.W && f.inc[fy * f.W + fx])
-            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, A.om);
+            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, A.om, 0.f);
         }
     }
     c.b[I] = s;
@@ -153,19 +156,19 @@ __device__ void mg_up(const MgArgs& A, int l, int i0, int stride) {
   for (int a = i0; a < n; a += stride) {
     if (f.lab[a] < 0) { f.e[a] = 0.f; continue; }
     const int y = a / f.W, x = a - y * f.W;
-    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, A.om, A.sc);
+    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, A.om, A.sc, 0.f);
     float s = 0.f;
     const float w0 = f.wr[a];
-    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, A.om, A.sc));
+    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, A.om, A.sc, 0.f));
     if (x > 0) {
       const float w1 = f.wr[a - 1];
-      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, A.om, A.sc));
+      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, A.om, A.sc, 0.f));
     }
     const float w2 = f.wd[a];
-    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, A.om, A.sc));
+    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, A.om, A.sc, 0.f));
     if (y > 0) {
       const float w3 = f.wd[a - f.W];
-      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, A.om, A.sc));
+      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, A.om, A.sc, 0.f));
     }
     f.e[a] = za + A.om * f.invd[a] * (f.b[a] - s);
   }
@@ -213,6 +216,15 @@ __device__ __forceinline__ bool comp_now(const MgArgs& A, int c, int k) {
   return was && k < A.maxit && bb[c] > 0.0 && rr[c] > A.tol2 * bb[c];
 }
 
+// mean of the residual of component c at iteration k: projected out of r
+// before the V-cycle (the float32 updates of r let a constant, which no
+// operator step can remove, creep into each component's residual)
+__device__ __forceinline__ float comp_mean(const MgArgs& A, int c, int k) {
+  if (!A.project) return 0.f;
+  const double n = A.cs[11 * (size_t)A.Kc + c];
+  return n > 0.0 ? (float)(A.cs[(size_t)(12 + (k & 1)) * A.Kc + c] / n) : 0.f;
+}
+
 // level-0 restriction for the tile t: each of the 256 threads owns one level-1
 // cell of the tile (16 x 16 cells)
 template <bool CHECK>
@@ -225,13 +237,14 @@ __device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k) {
   const int lc = A.clab[A.loff[1] + I];
   float s = 0.f;
   if (lc >= 0 && (!CHECK || comp_now(A, lc, k))) {
+    const float mu = comp_mean(A, lc, k);
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
         const int fy = 2 * cy + dy, fx = 2 * cx + dx;
         if (fy < A.H && fx < A.W && A.inc0[fy * A.W + fx])
-          s += res_jac(A.r, A.invd, A.wr, A.wd, A.H, A.W, fy, fx, A.om);
+          s += res_jac(A.r, A.invd, A.wr, A.wd, A.H, A.W, fy, fx, A.om, mu);
       }
   }
   A.cb[A.loff[1] + I] = s;
@@ -263,6 +276,8 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   double* xb = A.cs + 8 * (size_t)Kc;
   double* xax = A.cs + 9 * (size_t)Kc;
   double* alph = A.cs + 10 * (size_t)Kc;
+  double* cnt = A.cs + 11 * (size_t)Kc;
+  double* srs = A.cs + 12 * (size_t)Kc;     // [2] sum of r
   int* act = A.ci;                          // [2]
   int* iters = A.ci + 2 * (size_t)Kc;
   int* err = &A.st->err;
@@ -299,7 +314,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     const float4 wu4 = up ? ldg<ALIGNED>(A.wd, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
     const float4 xd = dn ? ldg<ALIGNED>(A.x, g.a + W, g.nval) : make_float4(0, 0, 0, 0);
     float4 r4;
-    float pv[3][4];
+    float pv[3][4], pc[1][4];
     bool on[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -316,18 +331,23 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
         pv[0][j] = on[j] ? xa * f4get(b4, j) : 0.f;
         pv[1][j] = on[j] ? xa * ax : 0.f;
       } else {
-        pv[0][j] = 0.f;
+        pv[0][j] = ra;
         pv[1][j] = ra * ra;
       }
       pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
+      pc[0][j] = on[j] ? 1.f : 0.f;
     }
     stg<ALIGNED>(A.r, g.a, g.nval, r4);
     stg<ALIGNED>(A.pb1, g.a, g.nval, make_float4(0, 0, 0, 0));
-    double* const dst[3] = {A.warm ? xb : sx, A.warm ? xax : rrs, bb};
+    double* const dst[3] = {A.warm ? xb : srs, A.warm ? xax : rrs, bb};
     const int key = ul >= 0 ? ul : group_key(lab, on);
     float v[3];
     group_values<3>(key, lab, on, pv, dst, v);
     tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+    double* const dc[1] = {cnt};
+    float vc[1];
+    group_values<1>(key, lab, on, pc, dc, vc);
+    tile_accum<true, 1>(ul, key == -2 ? -1 : key, vc, dc, s_key, s_val, sh);
     if (threadIdx.x == 0) {
       const int pos = atomicAdd(&A.ntl[0], 1);
       A.tiles[pos] = make_int2(t, ul);
@@ -335,7 +355,6 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   }
   if (!grid_barrier(&A.st->bar, err)) return;
   const int nt = *(volatile int*)&A.ntl[0];
-  for (int c = gtid; c < K; c += gthr) sx[c] = 0.0;   // slot borrowed above when not warm
   if (A.warm) {
     // energy-optimal scale of the warm start per component (alpha = 0: cold start)
     for (int c = gtid; c < K; c += gthr) {
@@ -351,7 +370,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
       float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
       const float4 b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
-      float pv[1][4];
+      float pv[2][4];
       bool on[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -362,14 +381,15 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
         if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
         f4set(r4, j, ra);
         pv[0][j] = ra * ra;
+        pv[1][j] = ra;
       }
       stg<ALIGNED>(A.x, g.a, g.nval, x4);
       stg<ALIGNED>(A.r, g.a, g.nval, r4);
-      double* const dst[1] = {rrs};
+      double* const dst[2] = {rrs, srs};
       const int key = ul >= 0 ? ul : group_key(lab, on);
-      float v[1];
-      group_values<1>(key, lab, on, pv, dst, v);
-      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+      float v[2];
+      group_values<2>(key, lab, on, pv, dst, v);
+      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
   }
@@ -422,7 +442,10 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     }
     // ---- level-0 prolongation and smoothing: z_k; r^T z per component
     if (gtid == 0) A.ntl[2 + Q] = 0;
-    for (int c = gtid; c < K; c += gthr) rrs[(size_t)Q * Kc + c] = 0.0;
+    for (int c = gtid; c < K; c += gthr) {
+      rrs[(size_t)Q * Kc + c] = 0.0;
+      srs[(size_t)Q * Kc + c] = 0.0;
+    }
     for (int i = blockIdx.x; i < nt; i += gridDim.x) {
       const int t = A.tiles[i].x, ul = A.tiles[i].y;
       if (ul >= 0 && !actk[ul]) continue;   // uniform across the CTA
@@ -437,7 +460,20 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       bool now[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && actk[lab[j]];
-      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+      const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+      // component means of r (once per label of the tile)
+      float mu[4];
+      {
+        int sl[4];
+        tile_slots(ul, lab, sl, s_lab);
+        if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0)
+          s_f[threadIdx.x * 4] = comp_mean(A, s_lab[threadIdx.x], k);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          mu[j] = sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? comp_mean(A, lab[j], k) : 0.f);
+      }
       const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
       const uchar4 in4 = ldinc<ALIGNED>(A.inc0, g.a, g.nval);
       // coarse corrections of the two level-1 cells under the thread's 4 pixels
@@ -450,16 +486,16 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       }
       float4 zc;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) f4set(zc, j, om * f4get(id4, j) * f4get(r4, j) + sc * ec[j]);
+      for (int j = 0; j < 4; ++j) f4set(zc, j, om * f4get(id4, j) * (f4get(r4, j) - mu[j]) + sc * ec[j]);
       float zl = __shfl_up_sync(NI_FULL, zc.w, 1), zr = __shfl_down_sync(NI_FULL, zc.x, 1);
       float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
       if (l8 == 0) {
         wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
-        zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc) : 0.f;
+        zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc, mu[0]) : 0.f;
       }
       if (l8 == 7)
         zr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f)
-                 ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc)
+                 ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc, mu[3])
                  : 0.f;
       float4 zu = make_float4(0, 0, 0, 0), zd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
       if (g.row > 0) {
@@ -470,7 +506,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (j < g.nval && f4get(wu4, j) != 0.f)
-            f4set(zu, j, om * f4get(iu, j) * f4get(ru, j) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+            f4set(zu, j, om * f4get(iu, j) * (f4get(ru, j) - mu[j]) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
       }
       if (g.row + 1 < H) {
         const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
@@ -479,7 +515,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if (j < g.nval && f4get(wd4, j) != 0.f)
-            f4set(zd, j, om * f4get(idd, j) * f4get(rd, j) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+            f4set(zd, j, om * f4get(idd, j) * (f4get(rd, j) - mu[j]) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
       }
       float4 z4;
       float pv[1][4];
@@ -490,9 +526,10 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
         const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
         const float az = f4get(wr4, j) * (za - zR) + f4get(wd4, j) * (za - f4get(zd, j)) + wl * (za - zL) +
                          f4get(wu4, j) * (za - f4get(zu, j));
-        const float zf = now[j] ? za + om * f4get(id4, j) * (f4get(r4, j) - az) : 0.f;
+        const float rp = now[j] ? f4get(r4, j) - mu[j] : f4get(r4, j);
+        const float zf = now[j] ? za + om * f4get(id4, j) * (rp - az) : 0.f;
         f4set(z4, j, zf);
-        pv[0][j] = zf * f4get(r4, j);
+        pv[0][j] = zf * rp;
       }
       stg<ALIGNED>(A.z, g.a, g.nval, z4);
       double* const dst[1] = {rz};
@@ -584,7 +621,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     }
     if (!grid_barrier(&A.st->bar, err)) return;
 
-    // ---- phase B: alpha_k; x += alpha p; r -= alpha q; r^T r per component
+    // ---- phase B: alpha_k; x += alpha p; r = (r - mean) - alpha q; r^T r, sum r per component
     for (int c = gtid; c < K; c += gthr) rzs[(size_t)Q * Kc + c] = 0.0;
     for (int i = blockIdx.x; i < nt; i += gridDim.x) {
       const int t = A.tiles[i].x, ul = A.tiles[i].y;
@@ -605,26 +642,41 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       const float4 p4 = ldg<ALIGNED>(pnew, g.a, g.nval), q4 = ldg<ALIGNED>(A.q, g.a, g.nval);
       int sl[4];
       tile_slots(ul, lab, sl, s_lab);
-      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) s_f[threadIdx.x * 4] = alphaf(s_lab[threadIdx.x]);
+      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) {
+        s_f[threadIdx.x * 4] = alphaf(s_lab[threadIdx.x]);
+        s_f[threadIdx.x * 4 + 1] = comp_mean(A, s_lab[threadIdx.x], k);
+      }
       __syncthreads();
-      float pv[1][4];
+      float pv[2][4];
       bool now[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         now[j] = lab[j] >= 0 && actk[lab[j]];
-        const float al = !now[j] ? 0.f : (sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? alphaf(lab[j]) : 0.f));
+        float al = 0.f, mu = 0.f;
+        if (now[j]) {
+          if (sl[j] >= 0) {
+            al = s_f[sl[j] * 4];
+            mu = s_f[sl[j] * 4 + 1];
+          } else if (sl[j] == -2) {
+            al = alphaf(lab[j]);
+            mu = comp_mean(A, lab[j], k);
+          }
+        }
         f4set(x4, j, f4get(x4, j) + al * f4get(p4, j));
-        const float ra = f4get(r4, j) - al * f4get(q4, j);
+        // r_{k+1} = (r_k - its component mean) - alpha q: the same projected
+        // residual the V-cycle of this iteration saw
+        const float ra = (f4get(r4, j) - mu) - al * f4get(q4, j);
         f4set(r4, j, ra);
         pv[0][j] = now[j] ? ra * ra : 0.f;
+        pv[1][j] = now[j] ? ra : 0.f;
       }
       stg<ALIGNED>(A.x, g.a, g.nval, x4);
       stg<ALIGNED>(A.r, g.a, g.nval, r4);
-      double* const dst[1] = {rrs + (size_t)Q * Kc};
+      double* const dst[2] = {rrs + (size_t)Q * Kc, srs + (size_t)Q * Kc};
       const int key = ul >= 0 ? ul : group_key(lab, now);
-      float v[1];
-      group_values<1>(key, lab, now, pv, dst, v);
-      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
+      float v[2];
+      group_values<2>(key, lab, now, pv, dst, v);
+      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
   }
@@ -824,7 +876,7 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NI_TILE_THREADS, 0);
   if (per_sm < 1) return ni_fail(h, NI_ERR_CUDA, "multigrid PCG: kernel cannot be resident");
-  const int want = h->cfg.tile_w > 0 ? h->cfg.tile_w : 4;
+  const int want = h->cfg.ctas_per_sm > 0 ? h->cfg.ctas_per_sm : 4;
   int grid = h->num_sms * std::min(per_sm, want);
   grid = std::max(1, std::min(grid, h->ntiles));
   cudaMemsetAsync(h->cacc, 0, sizeof(double) * 14 * (size_t)h->Kcap, s);
@@ -853,9 +905,10 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.warm = h->cfg.warm_start ? 1 : 0;
-  a.ncs = 4;
-  a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.67f;
-  a.sc = h->cfg.mg_correction > 0 ? (float)h->cfg.mg_correction : 1.5f;
+  a.ncs = h->cfg.mg_coarse_sweeps > 0 ? h->cfg.mg_coarse_sweeps : 4;
+  a.project = (h->cfg.mg_flags & 1) ? 1 : 0;
+  a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.8f;
+  a.sc = h->cfg.mg_correction > 0 ? (float)h->cfg.mg_correction : 1.0f;
   a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);

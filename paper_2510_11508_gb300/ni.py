@@ -39,8 +39,8 @@ class Config(C.Structure):
                 ("cg_maxit", C.c_int), ("scale_rtol", C.c_double), ("scale_maxit", C.c_int),
                 ("precision", C.c_int), ("batched", C.c_int), ("use_graph", C.c_int),
                 ("warm_start", C.c_int), ("hard_outliers", C.c_int), ("validate", C.c_int),
-                ("tile_w", C.c_int), ("tile_h", C.c_int), ("precond", C.c_int), ("mg_omega", C.c_double),
-                ("mg_correction", C.c_double), ("mg_cta_cells", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("mg_coarse_sweeps", C.c_int), ("precond", C.c_int), ("mg_omega", C.c_double),
+                ("mg_correction", C.c_double), ("mg_cta_cells", C.c_int), ("mg_flags", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -1,0 +1,98 @@
+"""Autotuner of the fill's launch shape and multigrid knobs.
+
+Runs ni_integrate on a caller's map for every point of a small search space and
+returns the configuration with the lowest median time whose labels are equal to
+the reference configuration's and whose log-depth agrees with it to `rtol`
+(the tuner never trades accuracy for speed).  Knobs:
+
+  ctas_per_sm       CTAs per SM of the persistent fill kernel (occupancy vs.
+                    grid-barrier cost);
+  mg_cta_cells      multigrid levels of at most this many cells run in one CTA
+                    (fewer grid barriers vs. serial work in that CTA);
+  mg_omega          damped-Jacobi weight of the V-cycle smoother;
+  mg_correction     scale of the coarse-grid correction.
+
+    python -m paper_2510_11508_gb300.tune --workload c3
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import os
+import sys
+from typing import Dict, Iterable, Optional
+
+import numpy as np
+import torch
+
+from . import ni
+
+SPACE = {
+    "ctas_per_sm": [2, 4],
+    "mg_cta_cells": [256, 1024, 4096, 16384],
+    "mg_omega": [0.67, 0.8, 0.9],
+    "mg_correction": [1.0],
+}
+
+
+def _time(it, n, m, reps):
+    ts = []
+    out = None
+    for _ in range(reps):
+        out = it.integrate(n, m, allow_unconverged=True)
+        ts.append(out[2]["ms_total"])
+    return float(np.median(ts)), out
+
+
+def tune(normals: torch.Tensor, mask: torch.Tensor, camera: Dict, params: Optional[Dict] = None,
+         space: Optional[Dict[str, Iterable]] = None, reps: int = 3, rtol: float = 1e-4, log=print):
+    """Grid search over `space` (default SPACE) with precond = 1; returns
+    (best knob dict, list of (knobs, ms, fill_iters))."""
+    H, W = mask.shape
+    space = dict(SPACE if space is None else space)
+    base = ni.Integrator(ni.config_for(H, W, camera, params, precond=1))
+    ms0, (d0, l0, s0) = _time(base, normals, mask, reps)
+    base.close()
+    l0 = l0.cpu().numpy()
+    z0 = torch.log(d0).cpu().numpy() if camera["camera"] == 1 else d0.cpu().numpy()
+    valid = mask.cpu().numpy() > 0
+    table = []
+    best, best_ms = {}, ms0
+    keys = list(space)
+    for vals in itertools.product(*(space[k] for k in keys)):
+        knobs = dict(zip(keys, vals))
+        it = ni.Integrator(ni.config_for(H, W, camera, params, precond=1, **knobs))
+        try:
+            ms, (d, l, s) = _time(it, normals, mask, reps)
+        finally:
+            it.close()
+        z = torch.log(d).cpu().numpy() if camera["camera"] == 1 else d.cpu().numpy()
+        dz = (z - z0)[valid]
+        dz = dz - dz.mean() if dz.size else dz
+        ok = (s["fill_unconverged"] == 0 and np.array_equal(l.cpu().numpy(), l0)
+              and (dz.size == 0 or float(np.sqrt(np.mean(dz * dz))) <= rtol))
+        table.append((knobs, ms, s["fill_iters"], ok))
+        log(f"{knobs} {ms:8.3f} ms fill_iters {s['fill_iters']:5d} {'ok' if ok else 'REJECTED'}")
+        if ok and ms < best_ms:
+            best, best_ms = knobs, ms
+    log(f"default {ms0:.3f} ms -> best {best_ms:.3f} ms with {best}")
+    return best, table
+
+
+def main():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    from synth import make_workload
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    w = make_workload(a.workload)
+    n = torch.from_numpy(w.normals).cuda()
+    m = torch.from_numpy(w.mask).cuda()
+    tune(n, m, w.camera, w.params, reps=a.reps)
+
+
+if __name__ == "__main__":
+    main()

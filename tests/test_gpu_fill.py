@@ -37,8 +37,9 @@ def _fill_pair(normals, mask, camera, params, **over):
 @pytest.mark.parametrize("batched", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_fill_matches_oracle(name, batched, precision):
+    """Jacobi preconditioner (plain global PCG or batched tile PCG)."""
     w = make_workload(name)
-    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=batched, precision=precision)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=batched, precision=precision, precond=0)
     m = w.mask > 0
     # per-component zero mean on both sides: compare directly
     d = (z - zr)[m]
@@ -51,7 +52,7 @@ def test_fill_matches_oracle(name, batched, precision):
 @pytest.mark.parametrize("batched", [0, 1])
 def test_fill_exact_plane(batched):
     nrm, mask, z, cam = G.plane_map(40, 53, G.PERSP, normal=(0.3, -0.2, -1.0), d=30.0, dtype=np.float32)
-    zf, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 5.0}, batched=batched)
+    zf, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 5.0}, batched=batched, precond=0)
     assert K == 1
     rms, mx = island_rms(zf, np.log(z), mask)
     assert rms < 2e-6, rms
@@ -60,7 +61,7 @@ def test_fill_exact_plane(batched):
 def test_fill_random_ragged_with_holes():
     nrm, mask, cam = G.random_normal_field(45, 77, n_dirs=2, jitter_deg=0.8, hole_frac=0.05, seed=3,
                                            block=9)
-    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1)
+    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=0)
     d = (z - zr)[mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
 
@@ -68,7 +69,7 @@ def test_fill_random_ragged_with_holes():
 def test_fill_irls_sweeps():
     w = make_workload("c3_small")
     p = dict(w.params, n_fill_irls=2)
-    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1, precond=0)
     d = (z - zr)[w.mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
 
@@ -123,3 +124,15 @@ def test_multigrid_needs_fewer_iterations():
         its[pc] = it.integrate(n, m)[2]["fill_iters"]
     print("fill iterations jacobi / multigrid", its)
     assert its[1] * 4 < its[0]
+
+
+@pytest.mark.parametrize("om,sc", [(0.67, 1.0), (0.8, 1.0), (0.9, 1.0)])
+def test_multigrid_knobs_converge(om, sc):
+    """The smoother weights the tuner may pick all converge on the 2048^2 map."""
+    w = make_workload("c3")
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params, precond=1, mg_omega=om, mg_correction=sc)
+    st = it.integrate(n, m)[2]
+    print("c3 multigrid", om, sc, "fill iterations", st["fill_iters"])
+    assert st["fill_unconverged"] == 0 and st["fill_iters"] < 400
