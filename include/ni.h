@@ -98,7 +98,8 @@ typedef struct {
                                symmetric V-cycle of aggregation multigrid on the pixel grid */
   double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.8) */
   double mg_correction;     /* scale of the coarse-grid correction (0: 1) */
-  int mg_cta_cells;         /* levels of at most this many cells run in one CTA (0: 4096) */
+  int mg_cta_cells;         /* coarse-level cells per CTA of a restriction/prolongation pass; the
+                               pass syncs only its CTAs (0: 256, one cell per thread) */
   int mg_flags;             /* bit 0: project each component's mean out of the residual
                                before the V-cycle */
 } ni_config;

@@ -155,6 +155,7 @@ struct ni_handle {
   float* mg_e = nullptr;       // coarse corrections
   uint8_t* mg_inc = nullptr;   // cell aggregated into its parent
   uint8_t* inc0 = nullptr;     // the same for the pixels
+  GridBar* mg_bar = nullptr;   // barriers of the coarse-level passes [2 * (NI_MG_MAX_LEVELS + 1)]
   float* z = nullptr;          // preconditioned residual
 
   DevState* st = nullptr;      // device
@@ -398,7 +399,8 @@ __device__ __forceinline__ void uf_unite(int* P, int a, int b) {
 // bounded: after NI_SPIN_LIMIT_CYCLES the block flags NI_DEV_ERR_TIMEOUT and
 // returns false (as it does when another block has flagged a timeout), so the
 // caller returns instead of hanging.
-__device__ __forceinline__ bool grid_barrier(GridBar* bar, int* err) {
+// grid_barrier_n: the same among the first n blocks (only they call it).
+__device__ __forceinline__ bool grid_barrier_n(GridBar* bar, unsigned int n, int* err) {
   __shared__ int s_fail;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -407,7 +409,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, int* err) {
     unsigned int g = *vgen;
     __threadfence();
     unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
-    if (arrived == gridDim.x) {
+    if (arrived == n) {
       atomicExch(&bar->count, 0u);
       __threadfence();
       atomicAdd(&bar->gen, 1u);
@@ -430,6 +432,10 @@ __device__ __forceinline__ bool grid_barrier(GridBar* bar, int* err) {
   int f = s_fail;
   __syncthreads();
   return f == 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(GridBar* bar, int* err) {
+  return grid_barrier_n(bar, gridDim.x, err);
 }
 
 __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldg(p); }

@@ -24,8 +24,10 @@
 //     operator, so CG with it converges like CG on a well-conditioned system.
 //
 // One cooperative persistent launch runs the whole solve.  Per iteration k:
-//   V-cycle on r_k minus its component mean (restriction of level 0 and the large levels by all CTAs,
-//   levels of at most `cta_cells` cells by CTA 0 alone), z_k and r_k^T z_k;
+//   V-cycle on r_k (restriction of level 0 by all CTAs, of the coarse levels
+//   by as many CTAs as their size calls for, with barriers among those only;
+//   the last levels, at most 512 cells, in CTA 0's shared memory), z_k and
+//   r_k^T z_k;
 //   phase A: p_k = z_k + beta_k p_{k-1}, q = A p_k, p^T A p per component;
 //   phase B: x += alpha p, r -= alpha q, r^T r per component.
 // Step lengths, convergence masks and iteration counts are per component, as
@@ -58,9 +60,13 @@ struct MgArgs {
   float* cb;
   float* ce;
   const uint8_t* cinc;
-  int L, Lc;
+  int L, Lc;               // levels Lc..L live in CTA 0's shared memory
   int lh[NI_MG_MAX_LEVELS + 1], lw[NI_MG_MAX_LEVELS + 1];
   long long loff[NI_MG_MAX_LEVELS + 1];
+  int smo[NI_MG_MAX_LEVELS + 1];   // offset of level l >= Lc in the shared arrays
+  int pd[NI_MG_MAX_LEVELS + 1];    // CTAs of the restriction from level l (l < Lc)
+  int pu[NI_MG_MAX_LEVELS + 1];    // CTAs of the prolongation to level l (l < Lc)
+  GridBar* mbar;                   // [0..L]: after restrictions, [NI_MG_MAX_LEVELS+1+l]: before prolongations
   double* cs;
   int* ci;
   int2* tiles;             // list of tiles with a valid pixel (tile, uniform label)
@@ -88,6 +94,24 @@ __device__ __forceinline__ Lv coarse_level(const MgArgs& A, int l) {
   const long long o = A.loff[l];
   v.lab = A.clab + o; v.wr = A.cwr + o; v.wd = A.cwd + o; v.invd = A.cinvd + o;
   v.b = A.cb + o; v.e = A.ce + o; v.inc = A.cinc + o;
+  v.H = A.lh[l]; v.W = A.lw[l];
+  return v;
+}
+
+#define MG_SMEM_CELLS 512
+
+// the small levels, held in shared memory by CTA 0
+struct MgSmem {
+  int lab[MG_SMEM_CELLS];
+  float wr[MG_SMEM_CELLS], wd[MG_SMEM_CELLS], invd[MG_SMEM_CELLS], b[MG_SMEM_CELLS], e[MG_SMEM_CELLS];
+  uint8_t inc[MG_SMEM_CELLS];
+};
+
+__device__ __forceinline__ Lv smem_level(const MgArgs& A, MgSmem& S, int l) {
+  Lv v;
+  const int o = A.smo[l];
+  v.lab = S.lab + o; v.wr = S.wr + o; v.wd = S.wd + o; v.invd = S.invd + o;
+  v.b = S.b + o; v.e = S.e + o; v.inc = S.inc + o;
   v.H = A.lh[l]; v.W = A.lw[l];
   return v;
 }
@@ -127,9 +151,8 @@ __device__ __forceinline__ float zc_at(const float* __restrict__ b, const float*
   return z;
 }
 
-// restriction of level l (>= 1) to level l+1 over cells i0, i0 + stride, ...
-__device__ void mg_down(const MgArgs& A, int l, int i0, int stride, const int* act) {
-  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+// restriction of level f (>= 1) to level c over cells i0, i0 + stride, ...
+__device__ void mg_down(const Lv& f, const Lv& c, float om, int i0, int stride, const int* act) {
   const int nc = c.H * c.W;
   for (int I = i0; I < nc; I += stride) {
     const int cy = I / c.W, cx = I - cy * c.W;
@@ -142,51 +165,72 @@ __device__ void mg_down(const MgArgs& A, int l, int i0, int stride, const int* a
         for (int dx = 0; dx < 2; ++dx) {
           const int fy = 2 * cy + dy, fx = 2 * cx + dx;
           if (fy < f.H && fx < f.W && f.inc[fy * f.W + fx])
-            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, A.om, 0.f);
+            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, om, 0.f);
         }
     }
     c.b[I] = s;
   }
 }
 
-// prolongation and post-smoothing on level l (>= 1): e_l from b_l and e_{l+1}
-__device__ void mg_up(const MgArgs& A, int l, int i0, int stride) {
-  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+// prolongation and post-smoothing on level f (>= 1): e_f from b_f and e_c
+__device__ void mg_up(const Lv& f, const Lv& c, float om, float sc, int i0, int stride) {
   const int n = f.H * f.W;
   for (int a = i0; a < n; a += stride) {
     if (f.lab[a] < 0) { f.e[a] = 0.f; continue; }
     const int y = a / f.W, x = a - y * f.W;
-    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, A.om, A.sc, 0.f);
+    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, om, sc, 0.f);
     float s = 0.f;
     const float w0 = f.wr[a];
-    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, A.om, A.sc, 0.f));
+    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, om, sc, 0.f));
     if (x > 0) {
       const float w1 = f.wr[a - 1];
-      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, A.om, A.sc, 0.f));
+      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, om, sc, 0.f));
     }
     const float w2 = f.wd[a];
-    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, A.om, A.sc, 0.f));
+    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, om, sc, 0.f));
     if (y > 0) {
       const float w3 = f.wd[a - f.W];
-      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, A.om, A.sc, 0.f));
+      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, om, sc, 0.f));
     }
-    f.e[a] = za + A.om * f.invd[a] * (f.b[a] - s);
+    f.e[a] = za + om * f.invd[a] * (f.b[a] - s);
   }
 }
 
-// the levels of at most cta_cells cells, in one CTA: restriction down to level
-// L, damped Jacobi steps there, prolongation and smoothing back up to level Lc
-__device__ void mg_cta_levels(const MgArgs& A, const int* act) {
+// CTA 0, once per launch: the constant data of levels Lc..L into shared memory
+__device__ void mg_smem_load(const MgArgs& A, MgSmem& S) {
+  for (int l = A.Lc; l <= A.L; ++l) {
+    const Lv g = coarse_level(A, l);
+    const int o = A.smo[l], n = g.H * g.W;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      S.lab[o + i] = g.lab[i];
+      S.wr[o + i] = g.wr[i];
+      S.wd[o + i] = g.wd[i];
+      S.invd[o + i] = g.invd[i];
+      S.inc[o + i] = l < A.L ? g.inc[i] : 0;
+    }
+  }
+  __syncthreads();
+}
+
+// CTA 0, every iteration: restriction from level Lc down to L, damped Jacobi
+// steps on level L (<= 4 cells), prolongation and smoothing back up to Lc, all
+// in shared memory; b_Lc comes from and e_Lc goes to global memory
+__device__ void mg_cta_levels(const MgArgs& A, MgSmem& S, const int* act) {
+  const Lv g = coarse_level(A, A.Lc);
+  const Lv t = smem_level(A, S, A.Lc);
+  const int n = g.H * g.W;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) t.b[i] = g.b[i];
+  __syncthreads();
   for (int l = A.Lc; l < A.L; ++l) {
-    mg_down(A, l, threadIdx.x, blockDim.x, act);
+    mg_down(smem_level(A, S, l), smem_level(A, S, l + 1), A.om, threadIdx.x, blockDim.x, act);
     __syncthreads();
   }
-  const Lv c = coarse_level(A, A.L);
+  const Lv c = smem_level(A, S, A.L);
   if (threadIdx.x == 0) {
     float e[4] = {0.f, 0.f, 0.f, 0.f}, en[4];
-    const int n = c.H * c.W;   // <= 4
+    const int nL = c.H * c.W;   // <= 4
     for (int it = 0; it < A.ncs; ++it) {
-      for (int a = 0; a < n; ++a) {
+      for (int a = 0; a < nL; ++a) {
         if (c.lab[a] < 0) { en[a] = 0.f; continue; }
         const int y = a / c.W, x = a - y * c.W;
         float s = 0.f;
@@ -196,15 +240,16 @@ __device__ void mg_cta_levels(const MgArgs& A, const int* act) {
         if (y > 0) s += c.wd[a - c.W] * (e[a] - e[a - c.W]);
         en[a] = e[a] + A.om * c.invd[a] * (c.b[a] - s);
       }
-      for (int a = 0; a < n; ++a) e[a] = en[a];
+      for (int a = 0; a < nL; ++a) e[a] = en[a];
     }
-    for (int a = 0; a < n; ++a) c.e[a] = e[a];
+    for (int a = 0; a < nL; ++a) c.e[a] = e[a];
   }
   __syncthreads();
   for (int l = A.L - 1; l >= A.Lc; --l) {
-    mg_up(A, l, threadIdx.x, blockDim.x);
+    mg_up(smem_level(A, S, l), smem_level(A, S, l + 1), A.om, A.sc, threadIdx.x, blockDim.x);
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) g.e[i] = t.e[i];
 }
 
 // active at iteration k (pure function of the state left by iteration k-1)
@@ -267,6 +312,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   __shared__ double s_val[TAB_SLOTS * 3];
   __shared__ int s_lab[TAB_SLOTS];
   __shared__ float s_f[TAB_SLOTS * 4];
+  __shared__ MgSmem s_mg;
   const int Kc = A.Kc, K = A.K, W = A.W, H = A.H, N = A.N;
   double* rzs = A.cs;                       // [2]
   double* pq = A.cs + 2 * (size_t)Kc;
@@ -291,6 +337,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     s_val[threadIdx.x * 3] = s_val[threadIdx.x * 3 + 1] = s_val[threadIdx.x * 3 + 2] = 0.0;
   }
   __syncthreads();
+  if (blockIdx.x == 0) mg_smem_load(A, s_mg);
 
   // ---- prologue: list of tiles with a valid pixel; r_0 = b - A x0; r^T r, b^T b
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
@@ -430,16 +477,22 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     if (!grid_barrier(&A.st->bar, err)) return;
     if (*(volatile int*)&A.ntl[2 + P] == 0) break;
     const int* actk = act + (size_t)P * Kc;
+    // restrictions of levels 1..Lc-1 on their first pd[l] CTAs (barriers among
+    // those only: the later, smaller passes run on subsets of them)
     for (int l = 1; l < A.Lc; ++l) {
-      mg_down(A, l, gtid, gthr, actk);
-      if (!grid_barrier(&A.st->bar, err)) return;
+      if (blockIdx.x >= A.pd[l]) break;
+      mg_down(coarse_level(A, l), coarse_level(A, l + 1), om, gtid, A.pd[l] * blockDim.x, actk);
+      if (!grid_barrier_n(&A.mbar[l], A.pd[l], err)) return;
     }
-    if (blockIdx.x == 0) mg_cta_levels(A, actk);
-    if (!grid_barrier(&A.st->bar, err)) return;
+    if (blockIdx.x == 0) mg_cta_levels(A, s_mg, actk);
+    // prolongations to levels Lc-1..1, each after a barrier among its own CTAs
+    // (which include the writers of the coarser correction)
     for (int l = A.Lc - 1; l >= 1; --l) {
-      mg_up(A, l, gtid, gthr);
-      if (!grid_barrier(&A.st->bar, err)) return;
+      if (blockIdx.x >= A.pu[l]) continue;
+      if (!grid_barrier_n(&A.mbar[NI_MG_MAX_LEVELS + 1 + l], A.pu[l], err)) return;
+      mg_up(coarse_level(A, l), coarse_level(A, l + 1), om, sc, gtid, A.pu[l] * blockDim.x);
     }
+    if (!grid_barrier(&A.st->bar, err)) return;
     // ---- level-0 prolongation and smoothing: z_k; r^T z per component
     if (gtid == 0) A.ntl[2 + Q] = 0;
     for (int c = gtid; c < K; c += gthr) {
@@ -828,6 +881,7 @@ static ni_status ensure_mg(ni_handle* h, cudaStream_t s) {
   al(&h->mg_lab, total); al(&h->mg_wr, total); al(&h->mg_wd, total); al(&h->mg_d, total);
   al(&h->mg_invd, total); al(&h->mg_b, total); al(&h->mg_e, total); al(&h->mg_inc, total);
   al(&h->inc0, (size_t)h->Npad); al(&h->z, (size_t)h->Npad);
+  al(&h->mg_bar, (size_t)2 * (NI_MG_MAX_LEVELS + 1));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return ni_fail(h, NI_ERR_OOM, "multigrid hierarchy allocation failed");
@@ -844,6 +898,8 @@ static ni_status ensure_mg(ni_handle* h, cudaStream_t s) {
 void free_mg(ni_handle* h) {
   cudaFree(h->mg_lab); cudaFree(h->mg_wr); cudaFree(h->mg_wd); cudaFree(h->mg_d); cudaFree(h->mg_invd);
   cudaFree(h->mg_b); cudaFree(h->mg_e); cudaFree(h->mg_inc); cudaFree(h->inc0); cudaFree(h->z);
+  cudaFree(h->mg_bar);
+  h->mg_bar = nullptr;
   h->mg_lab = nullptr; h->mg_wr = h->mg_wd = h->mg_d = h->mg_invd = h->mg_b = h->mg_e = nullptr;
   h->mg_inc = h->inc0 = nullptr; h->z = nullptr;
   h->mg_cells = 0;
@@ -891,17 +947,28 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   a.clab = h->mg_lab; a.cwr = h->mg_wr; a.cwd = h->mg_wd; a.cinvd = h->mg_invd; a.cb = h->mg_b; a.ce = h->mg_e;
   a.cinc = h->mg_inc;
   a.L = L;
-  // first level small enough for one CTA
+  // levels Lc..L: the coarsest levels whose cells fit CTA 0's shared arrays
+  auto cells = [&](int l) { return (long long)h->mg_h[l] * h->mg_w[l]; };
   int Lc = L;
-  const long long cta_cells = h->cfg.mg_cta_cells > 0 ? h->cfg.mg_cta_cells : 4096;
-  for (int l = 1; l <= L; ++l)
-    if ((long long)h->mg_h[l] * h->mg_w[l] <= cta_cells) { Lc = l; break; }
+  long long tail = cells(L);
+  while (Lc > 1 && tail + cells(Lc - 1) <= MG_SMEM_CELLS) tail += cells(--Lc);
   a.Lc = Lc;
+  const long long per_cta = h->cfg.mg_cta_cells > 0 ? h->cfg.mg_cta_cells : 256;
+  int so = 0;
   for (int l = 0; l <= NI_MG_MAX_LEVELS; ++l) {
     a.lh[l] = l <= L ? h->mg_h[l] : 0;
     a.lw[l] = l <= L ? h->mg_w[l] : 0;
     a.loff[l] = l <= L ? h->mg_off[l] : 0;
+    a.smo[l] = 0;
+    if (l >= Lc && l <= L) { a.smo[l] = so; so += (int)cells(l); }
+    a.pd[l] = a.pu[l] = grid;
+    if (l >= 1 && l < Lc) {
+      a.pd[l] = (int)std::max(1LL, std::min((long long)grid, (cells(l + 1) + per_cta - 1) / per_cta));
+      a.pu[l] = (int)std::max(1LL, std::min((long long)grid, (cells(l) + per_cta - 1) / per_cta));
+    }
   }
+  a.mbar = h->mg_bar;
+  cudaMemsetAsync(h->mg_bar, 0, sizeof(GridBar) * 2 * (NI_MG_MAX_LEVELS + 1), s);
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.warm = h->cfg.warm_start ? 1 : 0;

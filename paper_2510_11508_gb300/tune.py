@@ -7,8 +7,8 @@ the reference configuration's and whose log-depth agrees with it to `rtol`
 
   ctas_per_sm       CTAs per SM of the persistent fill kernel (occupancy vs.
                     grid-barrier cost);
-  mg_cta_cells      multigrid levels of at most this many cells run in one CTA
-                    (fewer grid barriers vs. serial work in that CTA);
+  mg_cta_cells      coarse-level cells per CTA of a multigrid pass (a pass syncs
+                    only its CTAs: fewer barrier arrivals vs. serial work);
   mg_omega          damped-Jacobi weight of the V-cycle smoother;
   mg_correction     scale of the coarse-grid correction.
 
@@ -29,7 +29,7 @@ from . import ni
 
 SPACE = {
     "ctas_per_sm": [2, 4],
-    "mg_cta_cells": [256, 1024, 4096, 16384],
+    "mg_cta_cells": [128, 256, 512],
     "mg_omega": [0.67, 0.8, 0.9],
     "mg_correction": [1.0],
 }
