@@ -359,22 +359,29 @@ def c5_map(H=8192, W=8192, n_cells=600, valid_frac=0.67, seed=1005, noise=0.01,
     nh = 0
     mask = np.ones((H, W), bool)
     coarse = 64
+    uc, vc = np.meshgrid(np.arange(0, W, coarse) + coarse / 2, np.arange(0, H, coarse) + coarse / 2)
+    keep = np.ones(uc.shape, bool)
     while True:
         cu, cv = rng.uniform(0, W), rng.uniform(0, H)
         a, b = rng.uniform(0.02, 0.08) * W, rng.uniform(0.02, 0.08) * H
         th = rng.uniform(0, math.pi)
         hole_c.append((cu, cv, a, b, th))
         nh += 1
-        # estimate on a coarse lattice
-        uc, vc = np.meshgrid(np.arange(0, W, coarse) + coarse / 2, np.arange(0, H, coarse) + coarse / 2)
-        keep = np.ones(uc.shape, bool)
-        for (hu, hv, ha, hb, ht) in hole_c:
-            c_, s_ = math.cos(ht), math.sin(ht)
-            x = (c_ * (uc - hu) + s_ * (vc - hv)) / ha
-            y = (-s_ * (uc - hu) + c_ * (vc - hv)) / hb
-            keep &= (x * x + y * y) > 1.0
+        # estimate on a coarse lattice (holes accumulate: test only the new one)
+        c_, s_ = math.cos(th), math.sin(th)
+        x = (c_ * (uc - cu) + s_ * (vc - cv)) / a
+        y = (-s_ * (uc - cu) + c_ * (vc - cv)) / b
+        keep &= (x * x + y * y) > 1.0
         if keep.mean() <= valid_frac or nh > 2000:
             break
+    # bounding box of each hole (2-pixel margin): outside it the ellipse test is true
+    hole_box = []
+    for (hu, hv, ha, hb, ht) in hole_c:
+        c_, s_ = math.cos(ht), math.sin(ht)
+        ex = math.sqrt((ha * c_) ** 2 + (hb * s_) ** 2)
+        ey = math.sqrt((ha * s_) ** 2 + (hb * c_) ** 2)
+        hole_box.append((max(0, int(math.floor(hu - ex)) - 2), min(W, int(math.ceil(hu + ex)) + 3),
+                         max(0, int(math.floor(hv - ey)) - 2), min(H, int(math.ceil(hv + ey)) + 3)))
     from scipy.spatial import cKDTree
     tree = cKDTree(sites)
     Z = np.full((H, W), np.nan)
@@ -386,11 +393,15 @@ def c5_map(H=8192, W=8192, n_cells=600, valid_frac=0.67, seed=1005, noise=0.01,
         r1 = min(H, r0 + chunk)
         v, u = np.mgrid[r0:r1, 0:W].astype(np.float64)
         m = np.ones(u.shape, bool)
-        for (hu, hv, ha, hb, ht) in hole_c:
+        for (hu, hv, ha, hb, ht), (x0, x1, y0, y1) in zip(hole_c, hole_box):
+            ya, yb = max(y0, r0), min(y1, r1)
+            if ya >= yb or x0 >= x1:
+                continue
+            uu, vv = u[ya - r0:yb - r0, x0:x1], v[ya - r0:yb - r0, x0:x1]
             c_, s_ = math.cos(ht), math.sin(ht)
-            x = (c_ * (u - hu) + s_ * (v - hv)) / ha
-            y = (-s_ * (u - hu) + c_ * (v - hv)) / hb
-            m &= (x * x + y * y) > 1.0
+            x = (c_ * (uu - hu) + s_ * (vv - hv)) / ha
+            y = (-s_ * (uu - hu) + c_ * (vv - hv)) / hb
+            m[ya - r0:yb - r0, x0:x1] &= (x * x + y * y) > 1.0
         pts = np.stack([u.ravel(), v.ravel()], 1)
         try:
             _, ci = tree.query(pts, k=1, workers=-1)
