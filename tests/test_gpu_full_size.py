@@ -1,0 +1,144 @@
+"""Full-size maps: the 8192 x 8192 map (4.4e7 valid pixels) and the 4096 x 4096
+evaluation map of the learned warm start (1.25e7 valid pixels), at the sizes
+and in the launch configuration the bench uses.
+
+Always run (the oracle computes these in well under a minute):
+  * seeding labels bit-exact against the oracle's seeding of the whole map;
+  * the fill of sampled components against the oracle's fill of a crop that
+    contains each of them with a margin (a component's fill system involves
+    only its own pixels, so the crop's answer is the full map's answer; the
+    crop keeps the rays by shifting the principal point);
+  * the whole pipeline runs, with the stop test, merges and output contract.
+With NI_FULL_SIZE=1: Algorithm 1 end to end against the oracle (minutes of
+CPU time and tens of GB of host memory)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synth import make_workload
+
+from gpu_util import dev, integrator, rel_depth_error
+
+pytestmark = pytest.mark.gpu
+
+_W = {}
+
+
+def _workload(name):
+    if name not in _W:
+        _W[name] = make_workload(name)
+    return _W[name]
+
+
+@pytest.mark.parametrize("name", ["c5"])
+def test_seed_labels_bit_exact_full_size(name):
+    w = _workload(name)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params)
+    lab, K = it.seed_components(n, m)
+    ref, Kr = O.seed_components(w.normals, w.mask, w.params["theta_c_deg"])
+    got = lab.cpu().numpy().reshape(-1)
+    it.close()
+    assert K == Kr
+    np.testing.assert_array_equal(got, ref)
+
+
+def _crop_fill(w, y0, y1, x0, x1):
+    cam = dict(w.camera)
+    cam["cx"] = cam["cx"] - x0
+    cam["cy"] = cam["cy"] - y0
+    nrm = np.ascontiguousarray(w.normals[y0:y1, x0:x1])
+    msk = np.ascontiguousarray(w.mask[y0:y1, x0:x1])
+    camo = O.Camera.from_dict(cam)
+    geo = O.geometry(nrm, msk, camo)
+    lab, K = O.seed_components(nrm, msk, w.params["theta_c_deg"])
+    z, _ = O.fill_components(geo, lab, K, w.params.get("k", 2.0), w.params.get("n_fill_irls", 1))
+    return z.reshape(msk.shape), lab.reshape(msk.shape)
+
+
+@pytest.mark.parametrize("name", ["c5"])
+def test_fill_sampled_components_full_size(name):
+    w = _workload(name)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params)
+    lab_d, K = it.seed_components(n, m)
+    z = it.solve_components().cpu().numpy()
+    lab = lab_d.cpu().numpy()
+    it.close()
+    # bounding boxes of all components
+    ys, xs = np.nonzero(lab >= 0)
+    ls = lab[ys, xs]
+    y0 = np.full(K, H); y1 = np.zeros(K, int); x0 = np.full(K, W); x1 = np.zeros(K, int)
+    np.minimum.at(y0, ls, ys); np.maximum.at(y1, ls, ys); np.minimum.at(x0, ls, xs); np.maximum.at(x1, ls, xs)
+    cnt = np.bincount(ls, minlength=K)
+    ext = np.maximum(y1 - y0, x1 - x0)
+    rng = np.random.default_rng(0)
+    # components of several sizes whose box fits a crop of at most 700 pixels a side
+    cand = np.nonzero((ext < 700) & (cnt >= 50))[0]
+    big = cand[np.argsort(-cnt[cand])][:2]
+    pick = np.unique(np.concatenate([big, rng.choice(cand, size=min(4, len(cand)), replace=False)]))
+    assert len(pick) >= 3
+    for c in pick:
+        cy0, cy1 = max(0, y0[c] - 2), min(H, y1[c] + 3)
+        cx0, cx1 = max(0, x0[c] - 2), min(W, x1[c] + 3)
+        zr, labr = _crop_fill(w, cy0, cy1, cx0, cx1)
+        sel = lab[cy0:cy1, cx0:cx1] == c
+        # the same pixel set is one component of the crop
+        lc = np.unique(labr[sel])
+        assert len(lc) == 1 and (labr == lc[0]).sum() == sel.sum()
+        zg = z[cy0:cy1, cx0:cx1][sel].astype(np.float64)
+        zo = zr[sel]
+        d = (zg - zg.mean()) - (zo - zo.mean())
+        rms = float(np.sqrt(np.mean(d * d)))
+        print(f"{name} component {c}: {cnt[c]} px, fill rms vs oracle crop {rms:.2e}")
+        assert rms <= 1e-4
+
+
+@pytest.mark.parametrize("name,warm", [("c5", 0), ("c5", 1), ("c4_eval", 0)])
+def test_pipeline_runs_full_size(name, warm, tmp_path):
+    from paper_2510_11508_gb300 import cnn
+    w = _workload(name)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params, warm_start=warm)
+    if warm:
+        net = cnn.Net(16, 256, seed=3)
+        path = str(tmp_path / "net.bin")
+        net.save(path)
+        it.load_net(path)
+    depth, labels, st = it.integrate(n, m)
+    d = depth.cpu().numpy()
+    it.close()
+    valid = w.mask > 0
+    print(name, "warm", warm, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "merges",
+                                                 "ms_seed", "ms_fill", "ms_scale", "ms_total",
+                                                 "warm_fallbacks")})
+    assert np.isfinite(d[valid]).all() and (d[valid] > 0).all()
+    assert np.isnan(d[~valid]).all()
+    assert 1 <= st["scale_iters"] <= w.params["T"]
+    assert st["K_final"] <= st["K0"]
+    if w.params["can_merge"] and st["scale_iters"] >= w.params["freq_merging"] + 1:
+        assert st["merges"] >= 1
+
+
+@pytest.mark.skipif(not os.environ.get("NI_FULL_SIZE"), reason="set NI_FULL_SIZE=1 (minutes of oracle time)")
+@pytest.mark.parametrize("name", ["c4_eval", "c5"])
+def test_full_oracle_parity_full_size(name):
+    w = _workload(name)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, w.params)
+    depth, labels, st = it.integrate(n, m)
+    ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(w.params))
+    err = rel_depth_error(np.nan_to_num(np.log(depth.cpu().numpy())), np.nan_to_num(ref["z"]), w.mask, 1)
+    print(name, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "ms_total")},
+          "oracle", ref["K0"], ref["K"], ref["iters"], "rel depth RMSE", err)
+    assert st["K0"] == ref["K0"]
+    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
+    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
+    assert err <= 1e-4
