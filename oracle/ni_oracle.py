@@ -309,8 +309,10 @@ def solve_min_norm(M, g):
     keep[first] = False
     x = np.zeros(n)
     if keep.any():
+        # symmetric minimum-degree ordering of M + M^T: the fill-in of a grid
+        # Laplacian stays near-linear, so maps of 1e7 pixels fit in host memory
         Mk = M[keep][:, keep].tocsc()
-        x[keep] = spsolve(Mk, np.asarray(g)[keep])
+        x[keep] = spsolve(Mk, np.asarray(g)[keep], permc_spec="MMD_AT_PLUS_A")
     return project_zero_mean(x, blk, nb)
 
 
