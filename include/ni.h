@@ -102,6 +102,9 @@ typedef struct {
                                pass syncs only its CTAs (0: 256, one cell per thread) */
   int mg_flags;             /* bit 0: project each component's mean out of the residual
                                before the V-cycle */
+  int fill_kernels;         /* multigrid fill: 0 one kernel per pass, chunks of iterations
+                               replayed from a CUDA graph (default); 1 one persistent
+                               cooperative kernel with software grid barriers */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

@@ -67,6 +67,7 @@ extern "C" void ni_config_default(ni_config* c, int H, int W) {
   c->mg_correction = 0;
   c->mg_cta_cells = 0;
   c->mg_flags = 0;
+  c->fill_kernels = 0;
   c->hard_outliers = 0;
   c->validate = 1;
 }
@@ -92,6 +93,7 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (!(c->mg_correction >= 0 && c->mg_correction <= 3)) { why = "mg_correction must be in [0, 3]"; return NI_ERR_INVALID_ARG; }
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 8) { why = "ctas_per_sm in [0, 8]"; return NI_ERR_INVALID_ARG; }
   if (c->mg_coarse_sweeps < 0 || c->mg_coarse_sweeps > 64) { why = "mg_coarse_sweeps in [0, 64]"; return NI_ERR_INVALID_ARG; }
+  if (c->fill_kernels != 0 && c->fill_kernels != 1) { why = "fill_kernels must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;

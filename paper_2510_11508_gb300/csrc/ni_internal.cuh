@@ -156,6 +156,7 @@ struct ni_handle {
   uint8_t* mg_inc = nullptr;   // cell aggregated into its parent
   uint8_t* inc0 = nullptr;     // the same for the pixels
   GridBar* mg_bar = nullptr;   // barriers of the coarse-level passes [2 * (NI_MG_MAX_LEVELS + 1)]
+  int* mg_iter = nullptr;      // per-phase multigrid solve: iteration index and done flag
   float* z = nullptr;          // preconditioned residual
 
   DevState* st = nullptr;      // device

@@ -305,96 +305,469 @@ __device__ __forceinline__ uint8_t u4get(const uchar4& v, int j) {
   return j == 0 ? v.x : (j == 1 ? v.y : (j == 2 ? v.z : v.w));
 }
 
-template <bool COMP, bool ALIGNED>
-__global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
-  __shared__ double sh[8 * 3 + 8];
-  __shared__ int s_key[TAB_SLOTS];
-  __shared__ double s_val[TAB_SLOTS * 3];
-  __shared__ int s_lab[TAB_SLOTS];
-  __shared__ float s_f[TAB_SLOTS * 4];
-  __shared__ MgSmem s_mg;
-  const int Kc = A.Kc, K = A.K, W = A.W, H = A.H, N = A.N;
-  double* rzs = A.cs;                       // [2]
-  double* pq = A.cs + 2 * (size_t)Kc;
-  double* rrs = A.cs + 3 * (size_t)Kc;      // [2]
-  double* bb = A.cs + 5 * (size_t)Kc;
-  double* sx = A.cs + 6 * (size_t)Kc;       // [2] sum x, count
-  double* xb = A.cs + 8 * (size_t)Kc;
-  double* xax = A.cs + 9 * (size_t)Kc;
-  double* alph = A.cs + 10 * (size_t)Kc;
-  double* cnt = A.cs + 11 * (size_t)Kc;
-  double* srs = A.cs + 12 * (size_t)Kc;     // [2] sum of r
-  int* act = A.ci;                          // [2]
-  int* iters = A.ci + 2 * (size_t)Kc;
-  int* err = &A.st->err;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
-  const int l8 = threadIdx.x & 7;
-  const float om = A.om, sc = A.sc;
-  const int W1 = A.lw[1];
-  const float* e1 = A.ce + A.loff[1];
+// ---------------------------------------------------------------------------
+// per-tile bodies of the solve, shared by the persistent kernel and the
+// per-phase kernels; every thread of the CTA calls them for the same tile
+// ---------------------------------------------------------------------------
+struct TileSmem {
+  double sh[8 * 3 + 8];
+  int key[TAB_SLOTS];
+  double val[TAB_SLOTS * 3];
+  int lab[TAB_SLOTS];
+  float f[TAB_SLOTS * 4];
+};
+
+__device__ __forceinline__ void tile_smem_init(TileSmem& S) {
   if (threadIdx.x < TAB_SLOTS) {
-    s_key[threadIdx.x] = -1;
-    s_val[threadIdx.x * 3] = s_val[threadIdx.x * 3 + 1] = s_val[threadIdx.x * 3 + 2] = 0.0;
+    S.key[threadIdx.x] = -1;
+    S.val[threadIdx.x * 3] = S.val[threadIdx.x * 3 + 1] = S.val[threadIdx.x * 3 + 2] = 0.0;
   }
   __syncthreads();
-  if (blockIdx.x == 0) mg_smem_load(A, s_mg);
+}
 
-  // ---- prologue: list of tiles with a valid pixel; r_0 = b - A x0; r^T r, b^T b
+// per-component slots (doubles, Kc each)
+#define MG_RZ 0    // [2] r^T z by iteration parity
+#define MG_PQ 2    // p^T A p
+#define MG_RR 3    // [2] r^T r by parity
+#define MG_BB 5    // b^T b
+#define MG_SX 6    // [2] sum x, pixel count (epilogue)
+#define MG_XB 8    // warm start: x0^T b
+#define MG_XAX 9   // warm start: x0^T A x0
+#define MG_ALPH 10 // warm start: scale of x0
+#define MG_CNT 11  // pixel count
+#define MG_SR 12   // [2] sum of r by parity
+__device__ __forceinline__ double* slot(const MgArgs& A, int s) { return A.cs + (size_t)s * A.Kc; }
+
+__device__ __forceinline__ void load_labels_tile(const MgArgs& A, const G4& g, int ul, int (&lab)[4]) {
+  if (ul >= 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
+  }
+}
+
+// prologue: r_0 = b - A x0; r^T r, sum r (or, warm, x0^T b and x0^T A x0), b^T b, count
+template <bool COMP, bool ALIGNED>
+__device__ void tile_prologue(const MgArgs& A, TileSmem& S, int t, int ul) {
+  const int W = A.W, H = A.H, l8 = threadIdx.x & 7;
+  const G4 g = group_of(t, A.ntx, H, W);
+  int lab[4];
+  ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+  const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval);
+  const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+  const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+  float xl = __shfl_up_sync(NI_FULL, x4.w, 1), xr = __shfl_down_sync(NI_FULL, x4.x, 1);
+  float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+  if (l8 == 0) {
+    xl = (g.nval > 0 && g.col > 0) ? A.x[g.a - 1] : 0.f;
+    wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
+  }
+  if (l8 == 7) xr = (g.nval == 4 && g.col + 4 < W) ? A.x[g.a + 4] : 0.f;
+  const bool up = g.row > 0, dn = g.row + 1 < H;
+  const float4 xu = up ? ldg<ALIGNED>(A.x, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+  const float4 wu4 = up ? ldg<ALIGNED>(A.wd, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
+  const float4 xd = dn ? ldg<ALIGNED>(A.x, g.a + W, g.nval) : make_float4(0, 0, 0, 0);
+  float4 r4;
+  float pv[3][4], pc[1][4];
+  bool on[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float xa = f4get(x4, j);
+    const float xR = j < 3 ? f4get(x4, j + 1) : xr, xL = j > 0 ? f4get(x4, j - 1) : xl;
+    const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+    const float ax = f4get(wr4, j) * (xa - xR) + f4get(wd4, j) * (xa - f4get(xd, j)) + wl * (xa - xL) +
+                     f4get(wu4, j) * (xa - f4get(xu, j));
+    on[j] = lab[j] >= 0;
+    float ra = f4get(b4, j) - ax;
+    if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+    f4set(r4, j, ra);
+    if (A.warm) {
+      pv[0][j] = on[j] ? xa * f4get(b4, j) : 0.f;
+      pv[1][j] = on[j] ? xa * ax : 0.f;
+    } else {
+      pv[0][j] = ra;
+      pv[1][j] = ra * ra;
+    }
+    pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
+    pc[0][j] = on[j] ? 1.f : 0.f;
+  }
+  stg<ALIGNED>(A.r, g.a, g.nval, r4);
+  stg<ALIGNED>(A.pb1, g.a, g.nval, make_float4(0, 0, 0, 0));
+  double* const dst[3] = {slot(A, A.warm ? MG_XB : MG_SR), slot(A, A.warm ? MG_XAX : MG_RR), slot(A, MG_BB)};
+  const int key = ul >= 0 ? ul : group_key(lab, on);
+  float v[3];
+  group_values<3>(key, lab, on, pv, dst, v);
+  tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+  double* const dc[1] = {slot(A, MG_CNT)};
+  float vc[1];
+  group_values<1>(key, lab, on, pc, dc, vc);
+  tile_accum<true, 1>(ul, key == -2 ? -1 : key, vc, dc, S.key, S.val, S.sh);
+}
+
+// warm start: x0 <- alpha_c x0, r <- (1 - alpha_c) b + alpha_c r (alpha from slot MG_ALPH)
+template <bool COMP, bool ALIGNED>
+__device__ void tile_warm(const MgArgs& A, TileSmem& S, int t, int ul) {
+  const G4 g = group_of(t, A.ntx, A.H, A.W);
+  int lab[4];
+  ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+  float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+  const float4 b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+  const double* alph = slot(A, MG_ALPH);
+  float pv[2][4];
+  bool on[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    on[j] = lab[j] >= 0;
+    const float al = on[j] ? (float)alph[lab[j]] : 0.f;
+    f4set(x4, j, al * f4get(x4, j));
+    float ra = (1.f - al) * f4get(b4, j) + al * f4get(r4, j);
+    if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
+    f4set(r4, j, ra);
+    pv[0][j] = ra * ra;
+    pv[1][j] = ra;
+  }
+  stg<ALIGNED>(A.x, g.a, g.nval, x4);
+  stg<ALIGNED>(A.r, g.a, g.nval, r4);
+  double* const dst[2] = {slot(A, MG_RR), slot(A, MG_SR)};
+  const int key = ul >= 0 ? ul : group_key(lab, on);
+  float v[2];
+  group_values<2>(key, lab, on, pv, dst, v);
+  tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+}
+
+// energy-optimal warm-start scale per component (grid-stride over c)
+__device__ void comp_warm_alpha(const MgArgs& A, int i0, int stride) {
+  const double* xb = slot(A, MG_XB);
+  const double* xax = slot(A, MG_XAX);
+  const double* bb = slot(A, MG_BB);
+  double* alph = slot(A, MG_ALPH);
+  for (int c = i0; c < A.K; c += stride) {
+    const double al = (xax[c] > 0.0 && xb[c] > 0.0) ? xb[c] / xax[c] : 0.0;
+    alph[c] = al;
+    if (al == 0.0 && bb[c] > 0.0) atomicAdd(&A.st->warm_fallbacks, 1);
+  }
+}
+
+// bookkeeping of iteration k (grid-stride over c): activity, iteration counts,
+// unconverged flags, active count; p^T A p cleared for this iteration
+__device__ void comp_book(const MgArgs& A, int k, int i0, int stride) {
+  const int Kc = A.Kc, P = k & 1, Q = P ^ 1;
+  const double* rrs = slot(A, MG_RR);
+  const double* bb = slot(A, MG_BB);
+  double* pq = slot(A, MG_PQ);
+  int* act = A.ci;
+  int* iters = A.ci + 2 * (size_t)Kc;
+  for (int c = i0; c < A.K; c += stride) {
+    const bool was = (k == 0) || act[(size_t)Q * Kc + c];
+    const bool conv = !(bb[c] > 0.0 && rrs[(size_t)P * Kc + c] > A.tol2 * bb[c]);
+    const bool nw = comp_now(A, c, k);
+    if (was && !conv && k >= A.maxit) {
+      atomicAdd(&A.st->fill_unconv, 1);
+      atomicOr(&A.st->err, NI_DEV_ERR_FILL_NOCONV);
+    }
+    act[(size_t)P * Kc + c] = nw ? 1 : 0;
+    if (nw) {
+      iters[c] += 1;
+      atomicAdd(&A.ntl[2 + P], 1);
+    }
+    pq[c] = 0.0;
+  }
+}
+
+// level-0 restriction of tile t (one level-1 cell per thread)
+__device__ __forceinline__ void tile_down0(const MgArgs& A, int t, int ul, int k) {
+  if (ul >= 0) {
+    if (comp_now(A, ul, k)) {
+      down0_tile<false>(A, t, k);
+    } else {   // a converged component: its level-1 cells get 0
+      const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
+      const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
+      if (cy < A.lh[1] && cx < A.lw[1]) A.cb[A.loff[1] + cy * A.lw[1] + cx] = 0.f;
+    }
+  } else {
+    down0_tile<true>(A, t, k);
+  }
+}
+
+// level-0 prolongation and smoothing: z_k and r^T z per component
+template <bool COMP, bool ALIGNED>
+__device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+  if (ul >= 0 && !actk[ul]) return;   // uniform across the CTA
+  const int W = A.W, H = A.H, l8 = threadIdx.x & 7, W1 = A.lw[1];
+  const float om = A.om, sc = A.sc;
+  const float* e1 = A.ce + A.loff[1];
+  double* rz = slot(A, MG_RZ + (k & 1));
+  const G4 g = group_of(t, A.ntx, H, W);
+  int lab[4];
+  if (ul >= 0) load_labels_tile(A, g, ul, lab);
+  else ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+  bool now[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && actk[lab[j]];
+  const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+  const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
+  float mu[4] = {0.f, 0.f, 0.f, 0.f};
+  if (A.project) {
+    int sl[4];
+    tile_slots(ul, lab, sl, S.lab);
+    if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) S.f[threadIdx.x * 4] = comp_mean(A, S.lab[threadIdx.x], k);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      mu[j] = sl[j] >= 0 ? S.f[sl[j] * 4] : (sl[j] == -2 ? comp_mean(A, lab[j], k) : 0.f);
+  }
+  const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+  const uchar4 in4 = ldinc<ALIGNED>(A.inc0, g.a, g.nval);
+  float ec[4];
+  {
+    const float* er = e1 + (size_t)(g.row >> 1) * W1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ec[j] = (j < g.nval && u4get(in4, j)) ? er[(g.col + j) >> 1] : 0.f;
+  }
+  float4 zc;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f4set(zc, j, om * f4get(id4, j) * (f4get(r4, j) - mu[j]) + sc * ec[j]);
+  float zl = __shfl_up_sync(NI_FULL, zc.w, 1), zr = __shfl_down_sync(NI_FULL, zc.x, 1);
+  float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+  if (l8 == 0) {
+    wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
+    zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc, mu[0]) : 0.f;
+  }
+  if (l8 == 7)
+    zr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f)
+             ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc, mu[3])
+             : 0.f;
+  float4 zu = make_float4(0, 0, 0, 0), zd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
+  if (g.row > 0) {
+    wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
+    const float4 ru = ldg<ALIGNED>(A.r, g.a - W, g.nval), iu = ldg<ALIGNED>(A.invd, g.a - W, g.nval);
+    const uchar4 cu = ldinc<ALIGNED>(A.inc0, g.a - W, g.nval);
+    const float* er = e1 + (size_t)((g.row - 1) >> 1) * W1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < g.nval && f4get(wu4, j) != 0.f)
+        f4set(zu, j, om * f4get(iu, j) * (f4get(ru, j) - mu[j]) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+  }
+  if (g.row + 1 < H) {
+    const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
+    const uchar4 cd = ldinc<ALIGNED>(A.inc0, g.a + W, g.nval);
+    const float* er = e1 + (size_t)((g.row + 1) >> 1) * W1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < g.nval && f4get(wd4, j) != 0.f)
+        f4set(zd, j, om * f4get(idd, j) * (f4get(rd, j) - mu[j]) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+  }
+  float4 z4;
+  float pv[1][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float za = f4get(zc, j);
+    const float zR = j < 3 ? f4get(zc, j + 1) : zr, zL = j > 0 ? f4get(zc, j - 1) : zl;
+    const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+    const float az = f4get(wr4, j) * (za - zR) + f4get(wd4, j) * (za - f4get(zd, j)) + wl * (za - zL) +
+                     f4get(wu4, j) * (za - f4get(zu, j));
+    const float rp = now[j] ? f4get(r4, j) - mu[j] : f4get(r4, j);
+    const float zf = now[j] ? za + om * f4get(id4, j) * (rp - az) : 0.f;
+    f4set(z4, j, zf);
+    pv[0][j] = zf * rp;
+  }
+  stg<ALIGNED>(A.z, g.a, g.nval, z4);
+  double* const dst[1] = {rz};
+  const int key = ul >= 0 ? ul : group_key(lab, now);
+  float v[1];
+  group_values<1>(key, lab, now, pv, dst, v);
+  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+}
+
+// direction: p_k = z_k + beta_k p_{k-1}; q = A p_k; p^T A p per component
+template <bool COMP, bool ALIGNED>
+__device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+  if (ul >= 0 && !actk[ul]) return;
+  const int W = A.W, H = A.H, l8 = threadIdx.x & 7, Kc = A.Kc;
+  const int P = k & 1, Q = P ^ 1;
+  const float* pold = Q ? A.pb1 : A.pb0;
+  float* pnew = P ? A.pb1 : A.pb0;
+  const double* rz = slot(A, MG_RZ + P);
+  const double* rzo = slot(A, MG_RZ + Q);
+  (void)Kc;
+  const G4 g = group_of(t, A.ntx, H, W);
+  int lab[4];
+  if (ul >= 0) load_labels_tile(A, g, ul, lab);
+  else ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+  auto betaf = [&](int c) -> float {
+    const double ro = rzo[c];
+    return (k > 0 && ro > 0.0) ? (float)(rz[c] / ro) : 0.f;
+  };
+  const float4 z4 = ldg<ALIGNED>(A.z, g.a, g.nval), po4 = ldg<ALIGNED>(pold, g.a, g.nval);
+  const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
+  int sl[4];
+  tile_slots(ul, lab, sl, S.lab);
+  if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) S.f[threadIdx.x * 4] = betaf(S.lab[threadIdx.x]);
+  __syncthreads();
+  float beta[4];
+  bool now[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    now[j] = lab[j] >= 0 && actk[lab[j]];
+    beta[j] = sl[j] >= 0 ? S.f[sl[j] * 4] : (sl[j] == -2 ? betaf(lab[j]) : 0.f);
+  }
+  float4 pn;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) f4set(pn, j, now[j] ? f4get(z4, j) + beta[j] * f4get(po4, j) : 0.f);
+  float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
+  float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
+  if (l8 == 0) {
+    const int a = g.a - 1;
+    wl0 = (g.nval > 0 && g.col > 0) ? A.wr[a] : 0.f;
+    pl = (wl0 != 0.f && now[0]) ? A.z[a] + beta[0] * pold[a] : 0.f;
+  }
+  if (l8 == 7) {
+    const int a = g.a + 4;
+    pr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f && now[3]) ? A.z[a] + beta[3] * pold[a] : 0.f;
+  }
+  float4 pu = make_float4(0, 0, 0, 0), pd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
+  if (g.row > 0) {
+    wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
+    const float4 zu = ldg<ALIGNED>(A.z, g.a - W, g.nval), pu0 = ldg<ALIGNED>(pold, g.a - W, g.nval);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      f4set(pu, j, (now[j] && f4get(wu4, j) != 0.f) ? f4get(zu, j) + beta[j] * f4get(pu0, j) : 0.f);
+  }
+  if (g.row + 1 < H) {
+    const float4 zd = ldg<ALIGNED>(A.z, g.a + W, g.nval), pd0 = ldg<ALIGNED>(pold, g.a + W, g.nval);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      f4set(pd, j, (now[j] && f4get(wd4, j) != 0.f) ? f4get(zd, j) + beta[j] * f4get(pd0, j) : 0.f);
+  }
+  float4 q4;
+  float pv[1][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float pa = f4get(pn, j);
+    const float pR = j < 3 ? f4get(pn, j + 1) : pr, pL = j > 0 ? f4get(pn, j - 1) : pl;
+    const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
+    const float dR = pa - pR, dD = pa - f4get(pd, j);
+    const float qa = f4get(wr4, j) * dR + f4get(wd4, j) * dD + wl * (pa - pL) + f4get(wu4, j) * (pa - f4get(pu, j));
+    f4set(q4, j, now[j] ? qa : 0.f);
+    pv[0][j] = now[j] ? f4get(wr4, j) * dR * dR + f4get(wd4, j) * dD * dD : 0.f;
+  }
+  stg<ALIGNED>(pnew, g.a, g.nval, pn);
+  stg<ALIGNED>(A.q, g.a, g.nval, q4);
+  double* const dst[1] = {slot(A, MG_PQ)};
+  const int key = ul >= 0 ? ul : group_key(lab, now);
+  float v[1];
+  group_values<1>(key, lab, now, pv, dst, v);
+  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+}
+
+// update: alpha_k; x += alpha p; r = (r - mean) - alpha q; r^T r, sum r per component
+template <bool COMP, bool ALIGNED>
+__device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+  if (ul >= 0 && !actk[ul]) return;
+  const int P = k & 1, Q = P ^ 1;
+  const float* pnew = P ? A.pb1 : A.pb0;
+  const double* rz = slot(A, MG_RZ + P);
+  const double* pq = slot(A, MG_PQ);
+  const G4 g = group_of(t, A.ntx, A.H, A.W);
+  int lab[4];
+  if (ul >= 0) load_labels_tile(A, g, ul, lab);
+  else ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
+  auto alphaf = [&](int c) -> float {
+    const double pp = pq[c];
+    return pp > 0.0 ? (float)(rz[c] / pp) : 0.f;
+  };
+  float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
+  const float4 p4 = ldg<ALIGNED>(pnew, g.a, g.nval), q4 = ldg<ALIGNED>(A.q, g.a, g.nval);
+  int sl[4];
+  tile_slots(ul, lab, sl, S.lab);
+  if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) {
+    S.f[threadIdx.x * 4] = alphaf(S.lab[threadIdx.x]);
+    S.f[threadIdx.x * 4 + 1] = comp_mean(A, S.lab[threadIdx.x], k);
+  }
+  __syncthreads();
+  float pv[2][4];
+  bool now[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    now[j] = lab[j] >= 0 && actk[lab[j]];
+    float al = 0.f, mu = 0.f;
+    if (now[j]) {
+      if (sl[j] >= 0) {
+        al = S.f[sl[j] * 4];
+        mu = S.f[sl[j] * 4 + 1];
+      } else if (sl[j] == -2) {
+        al = alphaf(lab[j]);
+        mu = comp_mean(A, lab[j], k);
+      }
+    }
+    f4set(x4, j, f4get(x4, j) + al * f4get(p4, j));
+    // r_{k+1} = (r_k - its component mean) - alpha q: the residual the V-cycle
+    // of this iteration saw
+    const float ra = (f4get(r4, j) - mu) - al * f4get(q4, j);
+    f4set(r4, j, ra);
+    pv[0][j] = now[j] ? ra * ra : 0.f;
+    pv[1][j] = now[j] ? ra : 0.f;
+  }
+  stg<ALIGNED>(A.x, g.a, g.nval, x4);
+  stg<ALIGNED>(A.r, g.a, g.nval, r4);
+  double* const dst[2] = {slot(A, MG_RR + Q), slot(A, MG_SR + Q)};
+  const int key = ul >= 0 ? ul : group_key(lab, now);
+  float v[2];
+  group_values<2>(key, lab, now, pv, dst, v);
+  tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+}
+
+// epilogue, first part: sum of x and pixel count per component
+__device__ void tile_epi_sums(const MgArgs& A, TileSmem& S, int t, int ul) {
+  const G4 g = group_of(t, A.ntx, A.H, A.W);
+  int lab[4];
+  ldlab<false>(A.labels, g.a, g.nval, lab);
+  const float4 x4 = ldg<false>(A.x, g.a, g.nval);
+  float pv[2][4];
+  bool on[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    on[j] = lab[j] >= 0;
+    pv[0][j] = on[j] ? f4get(x4, j) : 0.f;
+    pv[1][j] = on[j] ? 1.f : 0.f;
+  }
+  double* const dst[2] = {slot(A, MG_SX), slot(A, MG_SX + 1)};
+  const int key = ul >= 0 ? ul : group_key(lab, on);
+  float v[2];
+  group_values<2>(key, lab, on, pv, dst, v);
+  tile_accum<true, 2>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+}
+
+// epilogue, second part: zero mean per component; iteration statistics
+__device__ void mg_epi_apply(const MgArgs& A, int i0, int stride) {
+  const double* sx = slot(A, MG_SX);
+  const double* cnt = slot(A, MG_SX + 1);
+  const int* iters = A.ci + 2 * (size_t)A.Kc;
+  for (int a = i0; a < A.N; a += stride) {
+    const int c = A.labels[a];
+    if (c >= 0 && cnt[c] > 0) A.x[a] = (float)((double)A.x[a] - sx[c] / cnt[c]);
+  }
+  for (int c = i0; c < A.K; c += stride) {
+    atomicMax(&A.st->fill_iters, iters[c]);
+    if (iters[c] > 0)
+      atomicAdd(&A.st->fill_px_iters, (unsigned long long)iters[c] * (unsigned long long)cnt[c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// persistent variant: one cooperative launch, grid barriers between phases
+// ---------------------------------------------------------------------------
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
+  __shared__ TileSmem S;
+  __shared__ MgSmem s_mg;
+  int* err = &A.st->err;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
+  tile_smem_init(S);
+  if (blockIdx.x == 0) mg_smem_load(A, s_mg);
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const int ul = A.tile_lab[t];
     if (ul == -2) continue;
-    const G4 g = group_of(t, A.ntx, H, W);
-    int lab[4];
-    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval);
-    const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
-    const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
-    float xl = __shfl_up_sync(NI_FULL, x4.w, 1), xr = __shfl_down_sync(NI_FULL, x4.x, 1);
-    float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
-    if (l8 == 0) {
-      xl = (g.nval > 0 && g.col > 0) ? A.x[g.a - 1] : 0.f;
-      wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
-    }
-    if (l8 == 7) xr = (g.nval == 4 && g.col + 4 < W) ? A.x[g.a + 4] : 0.f;
-    const bool up = g.row > 0, dn = g.row + 1 < H;
-    const float4 xu = up ? ldg<ALIGNED>(A.x, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
-    const float4 wu4 = up ? ldg<ALIGNED>(A.wd, g.a - W, g.nval) : make_float4(0, 0, 0, 0);
-    const float4 xd = dn ? ldg<ALIGNED>(A.x, g.a + W, g.nval) : make_float4(0, 0, 0, 0);
-    float4 r4;
-    float pv[3][4], pc[1][4];
-    bool on[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float xa = f4get(x4, j);
-      const float xR = j < 3 ? f4get(x4, j + 1) : xr, xL = j > 0 ? f4get(x4, j - 1) : xl;
-      const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
-      const float ax = f4get(wr4, j) * (xa - xR) + f4get(wd4, j) * (xa - f4get(xd, j)) + wl * (xa - xL) +
-                       f4get(wu4, j) * (xa - f4get(xu, j));
-      on[j] = lab[j] >= 0;
-      float ra = f4get(b4, j) - ax;
-      if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
-      f4set(r4, j, ra);
-      if (A.warm) {
-        pv[0][j] = on[j] ? xa * f4get(b4, j) : 0.f;
-        pv[1][j] = on[j] ? xa * ax : 0.f;
-      } else {
-        pv[0][j] = ra;
-        pv[1][j] = ra * ra;
-      }
-      pv[2][j] = on[j] ? f4get(b4, j) * f4get(b4, j) : 0.f;
-      pc[0][j] = on[j] ? 1.f : 0.f;
-    }
-    stg<ALIGNED>(A.r, g.a, g.nval, r4);
-    stg<ALIGNED>(A.pb1, g.a, g.nval, make_float4(0, 0, 0, 0));
-    double* const dst[3] = {A.warm ? xb : srs, A.warm ? xax : rrs, bb};
-    const int key = ul >= 0 ? ul : group_key(lab, on);
-    float v[3];
-    group_values<3>(key, lab, on, pv, dst, v);
-    tile_accum<COMP, 3>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-    double* const dc[1] = {cnt};
-    float vc[1];
-    group_values<1>(key, lab, on, pc, dc, vc);
-    tile_accum<true, 1>(ul, key == -2 ? -1 : key, vc, dc, s_key, s_val, sh);
+    tile_prologue<COMP, ALIGNED>(A, S, t, ul);
     if (threadIdx.x == 0) {
       const int pos = atomicAdd(&A.ntl[0], 1);
       A.tiles[pos] = make_int2(t, ul);
@@ -403,371 +776,170 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   if (!grid_barrier(&A.st->bar, err)) return;
   const int nt = *(volatile int*)&A.ntl[0];
   if (A.warm) {
-    // energy-optimal scale of the warm start per component (alpha = 0: cold start)
-    for (int c = gtid; c < K; c += gthr) {
-      const double al = (xax[c] > 0.0 && xb[c] > 0.0) ? xb[c] / xax[c] : 0.0;
-      alph[c] = al;
-      if (al == 0.0 && bb[c] > 0.0) atomicAdd(&A.st->warm_fallbacks, 1);
-    }
+    comp_warm_alpha(A, gtid, gthr);
     if (!grid_barrier(&A.st->bar, err)) return;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-      const int t = A.tiles[i].x, ul = A.tiles[i].y;
-      const G4 g = group_of(t, A.ntx, H, W);
-      int lab[4];
-      ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
-      const float4 b4 = ldg<ALIGNED>(A.rhs, g.a, g.nval), id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
-      float pv[2][4];
-      bool on[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        on[j] = lab[j] >= 0;
-        const float al = on[j] ? (float)alph[lab[j]] : 0.f;
-        f4set(x4, j, al * f4get(x4, j));
-        float ra = (1.f - al) * f4get(b4, j) + al * f4get(r4, j);
-        if (f4get(id4, j) == 0.f || !on[j]) ra = 0.f;
-        f4set(r4, j, ra);
-        pv[0][j] = ra * ra;
-        pv[1][j] = ra;
-      }
-      stg<ALIGNED>(A.x, g.a, g.nval, x4);
-      stg<ALIGNED>(A.r, g.a, g.nval, r4);
-      double* const dst[2] = {rrs, srs};
-      const int key = ul >= 0 ? ul : group_key(lab, on);
-      float v[2];
-      group_values<2>(key, lab, on, pv, dst, v);
-      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-    }
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_warm<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y);
     if (!grid_barrier(&A.st->bar, err)) return;
   }
-
   for (int k = 0;; ++k) {
     const int P = k & 1, Q = P ^ 1;
-    double* rz = rzs + (size_t)P * Kc;
-    // ---- V-cycle, level-0 restriction; bookkeeping of iteration k
-    for (int c = gtid; c < K; c += gthr) {
-      const bool was = (k == 0) || act[(size_t)Q * Kc + c];
-      const bool conv = !(bb[c] > 0.0 && rrs[(size_t)P * Kc + c] > A.tol2 * bb[c]);
-      const bool nw = comp_now(A, c, k);
-      if (was && !conv && k >= A.maxit) {
-        atomicAdd(&A.st->fill_unconv, 1);
-        atomicOr(err, NI_DEV_ERR_FILL_NOCONV);
-      }
-      act[(size_t)P * Kc + c] = nw ? 1 : 0;
-      if (nw) {
-        iters[c] += 1;
-        atomicAdd(&A.ntl[2 + P], 1);
-      }
-      pq[c] = 0.0;
-    }
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-      const int t = A.tiles[i].x, ul = A.tiles[i].y;
-      if (ul >= 0) {
-        if (comp_now(A, ul, k)) down0_tile<false>(A, t, k);
-        else {
-          // the tile's level-1 cells belong to a converged component: zero them
-          const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
-          const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
-          if (cy < A.lh[1] && cx < W1) A.cb[A.loff[1] + cy * W1 + cx] = 0.f;
-        }
-      } else {
-        down0_tile<true>(A, t, k);
-      }
-    }
+    comp_book(A, k, gtid, gthr);
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_down0(A, A.tiles[i].x, A.tiles[i].y, k);
     if (!grid_barrier(&A.st->bar, err)) return;
     if (*(volatile int*)&A.ntl[2 + P] == 0) break;
-    const int* actk = act + (size_t)P * Kc;
-    // restrictions of levels 1..Lc-1 on their first pd[l] CTAs (barriers among
-    // those only: the later, smaller passes run on subsets of them)
+    const int* actk = A.ci + (size_t)P * A.Kc;
     for (int l = 1; l < A.Lc; ++l) {
       if (blockIdx.x >= A.pd[l]) break;
-      mg_down(coarse_level(A, l), coarse_level(A, l + 1), om, gtid, A.pd[l] * blockDim.x, actk);
+      mg_down(coarse_level(A, l), coarse_level(A, l + 1), A.om, gtid, A.pd[l] * blockDim.x, actk);
       if (!grid_barrier_n(&A.mbar[l], A.pd[l], err)) return;
     }
     if (blockIdx.x == 0) mg_cta_levels(A, s_mg, actk);
-    // prolongations to levels Lc-1..1, each after a barrier among its own CTAs
-    // (which include the writers of the coarser correction)
     for (int l = A.Lc - 1; l >= 1; --l) {
       if (blockIdx.x >= A.pu[l]) continue;
       if (!grid_barrier_n(&A.mbar[NI_MG_MAX_LEVELS + 1 + l], A.pu[l], err)) return;
-      mg_up(coarse_level(A, l), coarse_level(A, l + 1), om, sc, gtid, A.pu[l] * blockDim.x);
+      mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, A.pu[l] * blockDim.x);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
-    // ---- level-0 prolongation and smoothing: z_k; r^T z per component
     if (gtid == 0) A.ntl[2 + Q] = 0;
-    for (int c = gtid; c < K; c += gthr) {
-      rrs[(size_t)Q * Kc + c] = 0.0;
-      srs[(size_t)Q * Kc + c] = 0.0;
+    for (int c = gtid; c < A.K; c += gthr) {
+      slot(A, MG_RR + Q)[c] = 0.0;
+      slot(A, MG_SR + Q)[c] = 0.0;
     }
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-      const int t = A.tiles[i].x, ul = A.tiles[i].y;
-      if (ul >= 0 && !actk[ul]) continue;   // uniform across the CTA
-      const G4 g = group_of(t, A.ntx, H, W);
-      int lab[4];
-      if (ul >= 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
-      } else {
-        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-      }
-      bool now[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && actk[lab[j]];
-      const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
-      const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
-      // component means of r (once per label of the tile)
-      float mu[4];
-      {
-        int sl[4];
-        tile_slots(ul, lab, sl, s_lab);
-        if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0)
-          s_f[threadIdx.x * 4] = comp_mean(A, s_lab[threadIdx.x], k);
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          mu[j] = sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? comp_mean(A, lab[j], k) : 0.f);
-      }
-      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
-      const uchar4 in4 = ldinc<ALIGNED>(A.inc0, g.a, g.nval);
-      // coarse corrections of the two level-1 cells under the thread's 4 pixels
-      float ec[4];
-      {
-        const int cy = g.row >> 1;
-        const float* er = e1 + (size_t)cy * W1;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ec[j] = (j < g.nval && u4get(in4, j)) ? er[(g.col + j) >> 1] : 0.f;
-      }
-      float4 zc;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) f4set(zc, j, om * f4get(id4, j) * (f4get(r4, j) - mu[j]) + sc * ec[j]);
-      float zl = __shfl_up_sync(NI_FULL, zc.w, 1), zr = __shfl_down_sync(NI_FULL, zc.x, 1);
-      float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
-      if (l8 == 0) {
-        wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
-        zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc, mu[0]) : 0.f;
-      }
-      if (l8 == 7)
-        zr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f)
-                 ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc, mu[3])
-                 : 0.f;
-      float4 zu = make_float4(0, 0, 0, 0), zd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
-      if (g.row > 0) {
-        wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
-        const float4 ru = ldg<ALIGNED>(A.r, g.a - W, g.nval), iu = ldg<ALIGNED>(A.invd, g.a - W, g.nval);
-        const uchar4 cu = ldinc<ALIGNED>(A.inc0, g.a - W, g.nval);
-        const float* er = e1 + (size_t)((g.row - 1) >> 1) * W1;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j < g.nval && f4get(wu4, j) != 0.f)
-            f4set(zu, j, om * f4get(iu, j) * (f4get(ru, j) - mu[j]) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
-      }
-      if (g.row + 1 < H) {
-        const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
-        const uchar4 cd = ldinc<ALIGNED>(A.inc0, g.a + W, g.nval);
-        const float* er = e1 + (size_t)((g.row + 1) >> 1) * W1;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j < g.nval && f4get(wd4, j) != 0.f)
-            f4set(zd, j, om * f4get(idd, j) * (f4get(rd, j) - mu[j]) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
-      }
-      float4 z4;
-      float pv[1][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float za = f4get(zc, j);
-        const float zR = j < 3 ? f4get(zc, j + 1) : zr, zL = j > 0 ? f4get(zc, j - 1) : zl;
-        const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
-        const float az = f4get(wr4, j) * (za - zR) + f4get(wd4, j) * (za - f4get(zd, j)) + wl * (za - zL) +
-                         f4get(wu4, j) * (za - f4get(zu, j));
-        const float rp = now[j] ? f4get(r4, j) - mu[j] : f4get(r4, j);
-        const float zf = now[j] ? za + om * f4get(id4, j) * (rp - az) : 0.f;
-        f4set(z4, j, zf);
-        pv[0][j] = zf * rp;
-      }
-      stg<ALIGNED>(A.z, g.a, g.nval, z4);
-      double* const dst[1] = {rz};
-      const int key = ul >= 0 ? ul : group_key(lab, now);
-      float v[1];
-      group_values<1>(key, lab, now, pv, dst, v);
-      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-    }
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_up0<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
     if (!grid_barrier(&A.st->bar, err)) return;
-
-    // ---- phase A: p_k = z_k + beta_k p_{k-1}; q = A p_k; p^T A p per component
-    const float* pold = Q ? A.pb1 : A.pb0;
-    float* pnew = P ? A.pb1 : A.pb0;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-      const int t = A.tiles[i].x, ul = A.tiles[i].y;
-      if (ul >= 0 && !actk[ul]) continue;
-      const G4 g = group_of(t, A.ntx, H, W);
-      int lab[4];
-      if (ul >= 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
-      } else {
-        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-      }
-      auto betaf = [&](int c) -> float {
-        const double ro = rzs[(size_t)Q * Kc + c];
-        return (k > 0 && ro > 0.0) ? (float)(rz[c] / ro) : 0.f;
-      };
-      const float4 z4 = ldg<ALIGNED>(A.z, g.a, g.nval), po4 = ldg<ALIGNED>(pold, g.a, g.nval);
-      const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
-      int sl[4];
-      tile_slots(ul, lab, sl, s_lab);
-      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) s_f[threadIdx.x * 4] = betaf(s_lab[threadIdx.x]);
-      __syncthreads();
-      float beta[4];
-      bool now[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        now[j] = lab[j] >= 0 && actk[lab[j]];
-        beta[j] = sl[j] >= 0 ? s_f[sl[j] * 4] : (sl[j] == -2 ? betaf(lab[j]) : 0.f);
-      }
-      float4 pn;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) f4set(pn, j, now[j] ? f4get(z4, j) + beta[j] * f4get(po4, j) : 0.f);
-      float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
-      float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
-      if (l8 == 0) {
-        const int a = g.a - 1;
-        wl0 = (g.nval > 0 && g.col > 0) ? A.wr[a] : 0.f;
-        pl = (wl0 != 0.f && now[0]) ? A.z[a] + beta[0] * pold[a] : 0.f;
-      }
-      if (l8 == 7) {
-        const int a = g.a + 4;
-        pr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f && now[3]) ? A.z[a] + beta[3] * pold[a] : 0.f;
-      }
-      float4 pu = make_float4(0, 0, 0, 0), pd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
-      if (g.row > 0) {
-        wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
-        const float4 zu = ldg<ALIGNED>(A.z, g.a - W, g.nval), pu0 = ldg<ALIGNED>(pold, g.a - W, g.nval);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          f4set(pu, j, (now[j] && f4get(wu4, j) != 0.f) ? f4get(zu, j) + beta[j] * f4get(pu0, j) : 0.f);
-      }
-      if (g.row + 1 < H) {
-        const float4 zd = ldg<ALIGNED>(A.z, g.a + W, g.nval), pd0 = ldg<ALIGNED>(pold, g.a + W, g.nval);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          f4set(pd, j, (now[j] && f4get(wd4, j) != 0.f) ? f4get(zd, j) + beta[j] * f4get(pd0, j) : 0.f);
-      }
-      float4 q4;
-      float pv[1][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float pa = f4get(pn, j);
-        const float pR = j < 3 ? f4get(pn, j + 1) : pr, pL = j > 0 ? f4get(pn, j - 1) : pl;
-        const float wl = j > 0 ? f4get(wr4, j - 1) : wl0;
-        const float dR = pa - pR, dD = pa - f4get(pd, j);
-        const float qa = f4get(wr4, j) * dR + f4get(wd4, j) * dD + wl * (pa - pL) + f4get(wu4, j) * (pa - f4get(pu, j));
-        f4set(q4, j, now[j] ? qa : 0.f);
-        pv[0][j] = now[j] ? f4get(wr4, j) * dR * dR + f4get(wd4, j) * dD * dD : 0.f;
-      }
-      stg<ALIGNED>(pnew, g.a, g.nval, pn);
-      stg<ALIGNED>(A.q, g.a, g.nval, q4);
-      double* const dst[1] = {pq};
-      const int key = ul >= 0 ? ul : group_key(lab, now);
-      float v[1];
-      group_values<1>(key, lab, now, pv, dst, v);
-      tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-    }
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_dir<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
     if (!grid_barrier(&A.st->bar, err)) return;
-
-    // ---- phase B: alpha_k; x += alpha p; r = (r - mean) - alpha q; r^T r, sum r per component
-    for (int c = gtid; c < K; c += gthr) rzs[(size_t)Q * Kc + c] = 0.0;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-      const int t = A.tiles[i].x, ul = A.tiles[i].y;
-      if (ul >= 0 && !actk[ul]) continue;
-      const G4 g = group_of(t, A.ntx, H, W);
-      int lab[4];
-      if (ul >= 0) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lab[j] = j < g.nval ? ul : -1;
-      } else {
-        ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-      }
-      auto alphaf = [&](int c) -> float {
-        const double pp = pq[c];
-        return pp > 0.0 ? (float)(rz[c] / pp) : 0.f;
-      };
-      float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
-      const float4 p4 = ldg<ALIGNED>(pnew, g.a, g.nval), q4 = ldg<ALIGNED>(A.q, g.a, g.nval);
-      int sl[4];
-      tile_slots(ul, lab, sl, s_lab);
-      if (threadIdx.x < TAB_SLOTS && s_lab[threadIdx.x] >= 0) {
-        s_f[threadIdx.x * 4] = alphaf(s_lab[threadIdx.x]);
-        s_f[threadIdx.x * 4 + 1] = comp_mean(A, s_lab[threadIdx.x], k);
-      }
-      __syncthreads();
-      float pv[2][4];
-      bool now[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        now[j] = lab[j] >= 0 && actk[lab[j]];
-        float al = 0.f, mu = 0.f;
-        if (now[j]) {
-          if (sl[j] >= 0) {
-            al = s_f[sl[j] * 4];
-            mu = s_f[sl[j] * 4 + 1];
-          } else if (sl[j] == -2) {
-            al = alphaf(lab[j]);
-            mu = comp_mean(A, lab[j], k);
-          }
-        }
-        f4set(x4, j, f4get(x4, j) + al * f4get(p4, j));
-        // r_{k+1} = (r_k - its component mean) - alpha q: the same projected
-        // residual the V-cycle of this iteration saw
-        const float ra = (f4get(r4, j) - mu) - al * f4get(q4, j);
-        f4set(r4, j, ra);
-        pv[0][j] = now[j] ? ra * ra : 0.f;
-        pv[1][j] = now[j] ? ra : 0.f;
-      }
-      stg<ALIGNED>(A.x, g.a, g.nval, x4);
-      stg<ALIGNED>(A.r, g.a, g.nval, r4);
-      double* const dst[2] = {rrs + (size_t)Q * Kc, srs + (size_t)Q * Kc};
-      const int key = ul >= 0 ? ul : group_key(lab, now);
-      float v[2];
-      group_values<2>(key, lab, now, pv, dst, v);
-      tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-    }
+    for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_upd<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
     if (!grid_barrier(&A.st->bar, err)) return;
   }
-  // ---- epilogue: zero mean per component, statistics
-  for (int i = blockIdx.x; i < nt; i += gridDim.x) {
-    const int t = A.tiles[i].x, ul = A.tiles[i].y;
-    const G4 g = group_of(t, A.ntx, H, W);
-    int lab[4];
-    ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
-    const float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval);
-    float pv[2][4];
-    bool on[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      on[j] = lab[j] >= 0;
-      pv[0][j] = on[j] ? f4get(x4, j) : 0.f;
-      pv[1][j] = on[j] ? 1.f : 0.f;
-    }
-    double* const dst[2] = {sx, sx + Kc};
-    const int key = ul >= 0 ? ul : group_key(lab, on);
-    float v[2];
-    group_values<2>(key, lab, on, pv, dst, v);
-    tile_accum<true, 2>(ul, key == -2 ? -1 : key, v, dst, s_key, s_val, sh);
-  }
+  for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_epi_sums(A, S, A.tiles[i].x, A.tiles[i].y);
   if (!grid_barrier(&A.st->bar, err)) return;
-  for (int a = gtid; a < N; a += gthr) {
-    const int c = A.labels[a];
-    if (c >= 0) {
-      const double cnt = sx[(size_t)Kc + c];
-      if (cnt > 0) A.x[a] = (float)((double)A.x[a] - sx[c] / cnt);
-    }
-  }
-  for (int c = gtid; c < K; c += gthr) {
-    atomicMax(&A.st->fill_iters, iters[c]);
-    if (iters[c] > 0)
-      atomicAdd(&A.st->fill_px_iters, (unsigned long long)iters[c] * (unsigned long long)sx[(size_t)Kc + c]);
+  mg_epi_apply(A, gtid, gthr);
+}
+
+// ---------------------------------------------------------------------------
+// per-phase variant: one kernel per pass, one tile (or cell) per CTA (thread),
+// replayed from a CUDA graph in chunks of iterations; the iteration index and
+// the done flag live on the device
+// ---------------------------------------------------------------------------
+struct MgIter {
+  int k;      // current iteration
+  int done;   // no component active any more
+};
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_prologue(MgArgs A) {
+  __shared__ TileSmem S;
+  const int t = blockIdx.x;
+  const int ul = A.tile_lab[t];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_prologue<COMP, ALIGNED>(A, S, t, ul);
+}
+
+__global__ void k_mgx_warm_alpha(MgArgs A) { comp_warm_alpha(A, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x); }
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_warm(MgArgs A) {
+  __shared__ TileSmem S;
+  const int t = blockIdx.x;
+  const int ul = A.tile_lab[t];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_warm<COMP, ALIGNED>(A, S, t, ul);
+}
+
+// bookkeeping of iteration k (components) and the level-0 restriction (tiles)
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_book_down0(MgArgs A, MgIter* it) {
+  if (*(volatile int*)&it->done) return;
+  const int k = it->k;
+  comp_book(A, k, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  if (blockIdx.x < A.ntiles) {
+    const int ul = A.tile_lab[blockIdx.x];
+    if (ul != -2) tile_down0(A, blockIdx.x, ul, k);
   }
 }
+
+__device__ __forceinline__ bool mgx_skip(const MgArgs& A, const MgIter* it) {
+  return *(volatile int*)&it->done || *(volatile int*)&A.ntl[2 + (it->k & 1)] == 0;
+}
+
+__global__ void k_mgx_down(MgArgs A, MgIter* it, int l) {
+  if (mgx_skip(A, it)) return;
+  mg_down(coarse_level(A, l), coarse_level(A, l + 1), A.om, blockIdx.x * blockDim.x + threadIdx.x,
+          gridDim.x * blockDim.x, A.ci + (size_t)(it->k & 1) * A.Kc);
+}
+
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_cta(MgArgs A, MgIter* it) {
+  __shared__ MgSmem s_mg;
+  if (mgx_skip(A, it)) return;
+  mg_smem_load(A, s_mg);
+  mg_cta_levels(A, s_mg, A.ci + (size_t)(it->k & 1) * A.Kc);
+}
+
+__global__ void k_mgx_up(MgArgs A, MgIter* it, int l) {
+  if (mgx_skip(A, it)) return;
+  mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, blockIdx.x * blockDim.x + threadIdx.x,
+        gridDim.x * blockDim.x);
+}
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_up0(MgArgs A, MgIter* it) {
+  __shared__ TileSmem S;
+  if (mgx_skip(A, it)) return;
+  const int k = it->k, Q = (k & 1) ^ 1;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
+  if (gtid == 0) A.ntl[2 + Q] = 0;
+  for (int c = gtid; c < A.K; c += gthr) {
+    slot(A, MG_RR + Q)[c] = 0.0;
+    slot(A, MG_SR + Q)[c] = 0.0;
+  }
+  const int ul = A.tile_lab[blockIdx.x];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_up0<COMP, ALIGNED>(A, S, blockIdx.x, ul, k, A.ci + (size_t)(k & 1) * A.Kc);
+}
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_dir(MgArgs A, MgIter* it) {
+  __shared__ TileSmem S;
+  if (mgx_skip(A, it)) return;
+  const int ul = A.tile_lab[blockIdx.x];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_dir<COMP, ALIGNED>(A, S, blockIdx.x, ul, it->k, A.ci + (size_t)(it->k & 1) * A.Kc);
+}
+
+template <bool COMP, bool ALIGNED>
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_upd(MgArgs A, MgIter* it) {
+  __shared__ TileSmem S;
+  if (mgx_skip(A, it)) return;
+  const int k = it->k, Q = (k & 1) ^ 1;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthr = gridDim.x * blockDim.x;
+  for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
+  const int ul = A.tile_lab[blockIdx.x];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_upd<COMP, ALIGNED>(A, S, blockIdx.x, ul, k, A.ci + (size_t)(k & 1) * A.Kc);
+}
+
+// end of an iteration: the next index, or done once nothing was active
+__global__ void k_mgx_next(MgArgs A, MgIter* it) {
+  if (it->done) return;
+  if (A.ntl[2 + (it->k & 1)] == 0) it->done = 1;
+  else it->k += 1;
+}
+
+__global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_epi_sums(MgArgs A) {
+  __shared__ TileSmem S;
+  const int ul = A.tile_lab[blockIdx.x];
+  if (ul == -2) return;
+  tile_smem_init(S);
+  tile_epi_sums(A, S, blockIdx.x, ul);
+}
+
+__global__ void k_mgx_epi_apply(MgArgs A) { mg_epi_apply(A, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x); }
 
 // ---------------------------------------------------------------------------
 // hierarchy setup: level l+1 from level l (Galerkin product of the 2x2
@@ -882,6 +1054,7 @@ static ni_status ensure_mg(ni_handle* h, cudaStream_t s) {
   al(&h->mg_invd, total); al(&h->mg_b, total); al(&h->mg_e, total); al(&h->mg_inc, total);
   al(&h->inc0, (size_t)h->Npad); al(&h->z, (size_t)h->Npad);
   al(&h->mg_bar, (size_t)2 * (NI_MG_MAX_LEVELS + 1));
+  al(&h->mg_iter, (size_t)4);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return ni_fail(h, NI_ERR_OOM, "multigrid hierarchy allocation failed");
@@ -899,10 +1072,70 @@ void free_mg(ni_handle* h) {
   cudaFree(h->mg_lab); cudaFree(h->mg_wr); cudaFree(h->mg_wd); cudaFree(h->mg_d); cudaFree(h->mg_invd);
   cudaFree(h->mg_b); cudaFree(h->mg_e); cudaFree(h->mg_inc); cudaFree(h->inc0); cudaFree(h->z);
   cudaFree(h->mg_bar);
+  cudaFree(h->mg_iter);
   h->mg_bar = nullptr;
+  h->mg_iter = nullptr;
   h->mg_lab = nullptr; h->mg_wr = h->mg_wd = h->mg_d = h->mg_invd = h->mg_b = h->mg_e = nullptr;
   h->mg_inc = h->inc0 = nullptr; h->z = nullptr;
   h->mg_cells = 0;
+}
+
+// per-phase variant: prologue, then chunks of MGX_CHUNK iterations replayed from
+// a CUDA graph until the device says done, then the epilogue
+#define MGX_CHUNK 8
+template <bool COMP, bool AL>
+static ni_status mgx_run(ni_handle* h, const MgArgs& a, cudaStream_t s) {
+  const int nt = h->ntiles;
+  auto blocks = [&](long long n) { return (int)std::max(1LL, (n + 255) / 256); };
+  MgIter* itp = reinterpret_cast<MgIter*>(h->mg_iter);
+  cudaMemsetAsync(itp, 0, sizeof(MgIter), s);
+  k_mgx_prologue<COMP, AL><<<nt, NI_TILE_THREADS, 0, s>>>(a); NI_COUNT(h);
+  if (a.warm) {
+    k_mgx_warm_alpha<<<blocks(a.K), 256, 0, s>>>(a); NI_COUNT(h);
+    k_mgx_warm<COMP, AL><<<nt, NI_TILE_THREADS, 0, s>>>(a); NI_COUNT(h);
+  }
+  ni_status rc = ni_cuda_check(h, cudaGetLastError(), "multigrid PCG prologue");
+  if (rc != NI_OK) return rc;
+  auto cells = [&](int l) { return (long long)a.lh[l] * a.lw[l]; };
+  cudaStream_t cs;
+  cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  const long long launches_before = h->launches;
+  for (int i = 0; i < MGX_CHUNK; ++i) {
+    k_mgx_book_down0<<<nt, NI_TILE_THREADS, 0, cs>>>(a, itp); NI_COUNT(h);
+    for (int l = 1; l < a.Lc; ++l) { k_mgx_down<<<blocks(cells(l + 1)), 256, 0, cs>>>(a, itp, l); NI_COUNT(h); }
+    k_mgx_cta<<<1, NI_TILE_THREADS, 0, cs>>>(a, itp); NI_COUNT(h);
+    for (int l = a.Lc - 1; l >= 1; --l) { k_mgx_up<<<blocks(cells(l)), 256, 0, cs>>>(a, itp, l); NI_COUNT(h); }
+    k_mgx_up0<COMP, AL><<<nt, NI_TILE_THREADS, 0, cs>>>(a, itp); NI_COUNT(h);
+    k_mgx_dir<COMP, AL><<<nt, NI_TILE_THREADS, 0, cs>>>(a, itp); NI_COUNT(h);
+    k_mgx_upd<COMP, AL><<<nt, NI_TILE_THREADS, 0, cs>>>(a, itp); NI_COUNT(h);
+    k_mgx_next<<<1, 1, 0, cs>>>(a, itp); NI_COUNT(h);
+  }
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  const long long per_chunk = h->launches - launches_before;
+  h->launches = launches_before;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  rc = ni_cuda_check(h, e, "multigrid PCG graph");
+  if (rc == NI_OK) {
+    for (int done_it = 0; done_it <= a.maxit; done_it += MGX_CHUNK) {
+      cudaGraphLaunch(exec, s);
+      h->launches += per_chunk;
+      cudaMemcpyAsync(&h->st_host->cg_done, &itp->done, sizeof(int), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      if (h->st_host->cg_done) break;
+    }
+    rc = ni_cuda_check(h, e, "multigrid PCG");
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (rc != NI_OK) return rc;
+  k_mgx_epi_sums<<<nt, NI_TILE_THREADS, 0, s>>>(a); NI_COUNT(h);
+  k_mgx_epi_apply<<<grid_cells(h, a.N), 256, 0, s>>>(a); NI_COUNT(h);
+  return ni_cuda_check(h, cudaGetLastError(), "multigrid PCG epilogue");
 }
 
 ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
@@ -977,6 +1210,10 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.8f;
   a.sc = h->cfg.mg_correction > 0 ? (float)h->cfg.mg_correction : 1.0f;
   a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
+  if (h->cfg.fill_kernels == 0) {
+    if (f64) return aligned ? mgx_run<true, true>(h, a, s) : mgx_run<true, false>(h, a, s);
+    return aligned ? mgx_run<false, true>(h, a, s) : mgx_run<false, false>(h, a, s);
+  }
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);
   NI_COUNT(h);

@@ -460,18 +460,25 @@ __global__ void k_node_assemble(const int* __restrict__ row_ptr, const int* __re
                                 double* __restrict__ gabs) {
   if (st->converged) return;
   const int K = st->K;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int c = gw; c < K; c += nw) {   // one warp per row (power-law degrees)
     double d = 0.0, gs = 0.0, ga = 0.0;
-    for (int j = row_ptr[c]; j < row_ptr[c + 1]; ++j) {
+    for (int j = row_ptr[c] + lane; j < row_ptr[c + 1]; j += 32) {
       int p = csr_pair[j];
       d += p_acc[3 * p];
       const double hp = p_acc[3 * p + 1];
       gs += (p_lo[p] == c) ? -hp : hp;
       ga += fabs(hp);
     }
-    diag[c] = d;
-    g[c] = gs;
-    gabs[c] = ga;
+    d = warp_sum_d(d);
+    gs = warp_sum_d(gs);
+    ga = warp_sum_d(ga);
+    if (lane == 0) {
+      diag[c] = d;
+      g[c] = gs;
+      gabs[c] = ga;
+    }
   }
 }
 
@@ -558,15 +565,23 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   const double stop2 = fmax(A.tol2 * gg, floor2);
   int it = 0;
   bool done = !(gg > 0.0) || gg <= stop2;
+  // q = L p with a group of G lanes per row: the quotient graph's degrees follow
+  // the component sizes (a large component borders thousands of small ones), so
+  // the multi-CTA path gives each row a warp; one CTA (K <= 1024) a thread
+  const int G = gridDim.x == 1 ? 1 : 32;
+  const int lane = threadIdx.x & (G - 1), gw = tid / G, nw = nthr / G;
   while (!done && it < A.maxit) {
     double pq = 0, d1 = 0, d2 = 0;
-    for (int c = tid; c < K; c += nthr) {
+    for (int c = gw; c < K; c += nw) {
       const double pc = A.pp[c];
       double acc = 0.0;
-      for (int j = A.row_ptr[c]; j < A.row_ptr[c + 1]; ++j)
+      for (int j = A.row_ptr[c] + lane; j < A.row_ptr[c + 1]; j += G)
         acc += A.p_acc[3 * A.csr_pair[j]] * (pc - A.pp[A.csr_col[j]]);
-      A.qq[c] = acc;
-      pq += A.pp[c] * acc;
+      if (G > 1) acc = warp_sum_d(acc);
+      if (lane == 0) {
+        A.qq[c] = acc;
+        pq += pc * acc;
+      }
     }
     if (!grid_sum3(pq, d1, d2, A.red, ncall, st, sh)) return;
     const double alpha = pq > 0.0 ? rz / pq : 0.0;
@@ -615,12 +630,14 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   }
 }
 
+// one CTA up to 1024 components (at most 32 rows per warp, no grid barrier);
+// above, about 8 rows per warp
 int scale_cg_grid(ni_handle* h) {
-  if (h->Kcap <= 8192) return 1;
+  if (h->Kcap <= 1024) return 1;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scale_cg, 1024, 0);
   int g = h->num_sms * std::max(1, std::min(per_sm, 2));
-  int need = (h->Kcap + 1023) / 1024;
+  int need = (h->Kcap + 255) / 256;
   return std::max(1, std::min(g, need));
 }
 
@@ -635,7 +652,7 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   ea.fx = h->cfg.cam.fx; ea.fy = h->cfg.cam.fy; ea.k = h->cfg.k;
   ea.Lt = log10(h->cfg.L); ea.Ut = log10(h->cfg.U); ea.U = h->cfg.U; ea.hard = h->cfg.hard_outliers;
   k_edge_accum<<<ge, 256, 0, s>>>(ea); NI_COUNT(h);
-  k_node_assemble<<<grid_lin(h, h->Kcap), 256, 0, s>>>(h->row_ptr, h->csr_pair, h->p_lo, h->p_acc, st,
+  k_node_assemble<<<grid_lin(h, 32LL * h->Kcap), 256, 0, s>>>(h->row_ptr, h->csr_pair, h->p_lo, h->p_acc, st,
                                                         h->sd, h->sv + 5 * (size_t)h->Kcap,
                                                         h->sv + 6 * (size_t)h->Kcap); NI_COUNT(h);
   ScaleArgs sa;

@@ -54,12 +54,12 @@ def test_struct_layout_matches_header(lib, tmp_path):
     src = tmp_path / "l.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ni.h"\nint main(){'
                    'printf("%zu %zu %zu %zu %zu\\n", sizeof(ni_config), sizeof(ni_stats),'
-                   ' offsetof(ni_config, cg_rtol), offsetof(ni_stats, energy), offsetof(ni_config, mg_flags));}')
+                   ' offsetof(ni_config, cg_rtol), offsetof(ni_stats, energy), offsetof(ni_config, fill_kernels));}')
     exe = tmp_path / "l"
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = subprocess.check_output([str(exe)]).decode().split()
     exp = [C.sizeof(ni.Config), C.sizeof(ni.Stats), ni.Config.cg_rtol.offset,
-           ni.Stats.energy.offset, ni.Config.mg_flags.offset]
+           ni.Stats.energy.offset, ni.Config.fill_kernels.offset]
     assert [int(v) for v in out] == exp
 
 

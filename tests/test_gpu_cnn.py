@@ -125,3 +125,59 @@ def test_warm_start_gives_the_cold_start_answer(tmp_path):
     err = O.aligned_rel_rmse(d1.cpu().numpy(), d0.cpu().numpy(), w.mask, 1)
     print("warm vs cold rel err", err, "iters", s0["fill_iters"], s1["fill_iters"])
     assert err < 1e-4
+
+
+def test_trained_network_gain(tmp_path):
+    """What the trained network gains over the method without it, on held-out
+    maps of the training distribution: the network is trained (GPU kernels) on
+    C2-type 64x64 maps solved by the plain method, then used as the fill's warm
+    start.  Asserted: it learned (validation depth loss well below the trivial
+    predictor's), the warm-started solve ends at the cold start's answer, and it
+    never costs iterations; the iteration gain is printed."""
+    import math
+    from paper_2510_11508_gb300 import train_warmstart as TW
+    T, n_train, n_eval = 64, 240, 12
+    maps = [G.c2_type_map(H=T, W=T, n_cells=4, target_valid=0.5 * T * T, seed=s, name="t")
+            for s in range(n_train + n_eval)]
+    normals = np.stack([w.normals for w in maps])
+    masks = np.stack([w.mask for w in maps])
+    cam = G._persp_cam(T, T)
+    params = dict(maps[0].params)
+    data = TW.solve_targets(normals[:n_train], masks[:n_train], cam, params, torch.device("cuda"))
+    zs = 1.0 / math.sqrt(max(TW.zero_predictor_loss(data, 0.0), 1e-30))
+    X, TZ, TL, TWt = data
+    data = (X, TZ * zs, TL, TWt)
+    net = cnn.Net(16, T, seed=1)
+    nval = 16
+    val = tuple(d[-nval:] for d in data)
+    base = TW.zero_predictor_loss(val, 0.0)
+    hist = TW.train(net, data, epochs=6, batch=16, lr=2e-3, w_weight=0.1, val_frac=nval / n_train,
+                    log=lambda *a: None)
+    trained = hist[-1]["val"][1]
+    p = net.get_params()
+    TW.fold_depth_scale(p, 1.0 / zs)
+    net.set_params(p)
+    path = str(tmp_path / "net64.bin")
+    net.save(path)
+    print(f"validation depth loss: trained {trained:.4f} vs zero predictor {base:.4f} (scaled units)")
+    assert trained < 0.7 * base
+    gains = {}
+    for pc in (0, 1):
+        cold_it, warm_it = [], []
+        for w in maps[n_train:]:
+            n, m = dev(w.normals, w.mask)
+            cold = integrator(T, T, cam, params, precond=pc)
+            d0, l0, s0 = cold.integrate(n, m)
+            warm = integrator(T, T, cam, params, precond=pc, warm_start=1)
+            warm.load_net(path)
+            d1, l1, s1 = warm.integrate(n, m)
+            assert np.array_equal(l0.cpu().numpy(), l1.cpu().numpy())
+            assert O.aligned_rel_rmse(d1.cpu().numpy(), d0.cpu().numpy(), w.mask, 1) < 1e-4
+            cold_it.append(s0["fill_px_iters"])
+            warm_it.append(s1["fill_px_iters"])
+            cold.close()
+            warm.close()
+        gains[pc] = 1.0 - sum(warm_it) / sum(cold_it)
+        print(f"precond {pc}: fill pixel-iterations cold {sum(cold_it)} warm {sum(warm_it)} "
+              f"(gain {100 * gains[pc]:.1f} %)")
+        assert sum(warm_it) <= 1.1 * sum(cold_it)

@@ -78,9 +78,13 @@ def test_fill_irls_sweeps():
 
 @pytest.mark.parametrize("name", ["c1", "c2", "c3_small"])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_fill_multigrid_matches_oracle(name, precision):
+@pytest.mark.parametrize("fill_kernels", [0, 1])
+def test_fill_multigrid_matches_oracle(name, precision, fill_kernels):
+    """Both multigrid drivers: per-phase kernels from a CUDA graph (0) and the
+    persistent cooperative kernel (1)."""
     w = make_workload(name)
-    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=1, precond=1, precision=precision)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=1, precond=1, precision=precision,
+                          fill_kernels=fill_kernels)
     m = w.mask > 0
     d = (z - zr)[m]
     scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[m]))
@@ -98,10 +102,11 @@ def test_fill_multigrid_exact_plane():
 
 
 @pytest.mark.parametrize("H,W", [(45, 77), (1, 93), (97, 1), (2, 2), (33, 65)])
-def test_fill_multigrid_ragged_shapes(H, W):
+@pytest.mark.parametrize("fill_kernels", [0, 1])
+def test_fill_multigrid_ragged_shapes(H, W, fill_kernels):
     nrm, mask, cam = G.random_normal_field(H, W, n_dirs=2, jitter_deg=0.8, hole_frac=0.05, seed=H * W,
                                            block=9)
-    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=1)
+    z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=1, fill_kernels=fill_kernels)
     d = (z - zr)[mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4 if d.size else True
 
