@@ -103,7 +103,7 @@ typedef struct {
   int mg_flags;             /* bit 0: project each component's mean out of the residual
                                before the V-cycle */
   int fill_kernels;         /* multigrid fill: 0 one kernel per pass, chunks of iterations
-                               replayed from a CUDA graph (default); 1 one persistent
+                               replayed from a CUDA graph; 1 (default) one persistent
                                cooperative kernel with software grid barriers */
 } ni_config;
 

@@ -67,7 +67,7 @@ extern "C" void ni_config_default(ni_config* c, int H, int W) {
   c->mg_correction = 0;
   c->mg_cta_cells = 0;
   c->mg_flags = 0;
-  c->fill_kernels = 0;
+  c->fill_kernels = 1;
   c->hard_outliers = 0;
   c->validate = 1;
 }

@@ -116,39 +116,81 @@ __device__ __forceinline__ Lv smem_level(const MgArgs& A, MgSmem& S, int l) {
   return v;
 }
 
-// (b_a - mu) - (A (om D^-1 (b - mu)))_a at cell (y, x) of a level: the residual
-// after one damped Jacobi step from zero (difference form of the stencil; mu is
-// the component's mean of b, projected out at level 0, 0 on coarse levels)
-__device__ __forceinline__ float res_jac(const float* __restrict__ b, const float* __restrict__ invd,
-                                         const float* __restrict__ wr, const float* __restrict__ wd, int H,
-                                         int W, int y, int x, float om, float mu) {
-  const int a = y * W + x;
-  const float ba = b[a] - mu;
-  const float ya = om * invd[a] * ba;
-  float s = 0.f;
-  const float w0 = wr[a];
-  if (w0 != 0.f) s += w0 * (ya - om * invd[a + 1] * (b[a + 1] - mu));
-  if (x > 0) {
-    const float w1 = wr[a - 1];
-    if (w1 != 0.f) s += w1 * (ya - om * invd[a - 1] * (b[a - 1] - mu));
-  }
-  const float w2 = wd[a];
-  if (w2 != 0.f) s += w2 * (ya - om * invd[a + W] * (b[a + W] - mu));
-  if (y > 0) {
-    const float w3 = wd[a - W];
-    if (w3 != 0.f) s += w3 * (ya - om * invd[a - W] * (b[a - W] - mu));
-  }
-  return ba - s;
-}
-
 // pre-smoothed value plus the scaled coarse correction at cell (y, x)
+// (all four loads issued together; (y, x) must lie inside the level)
 __device__ __forceinline__ float zc_at(const float* __restrict__ b, const float* __restrict__ invd,
                                        const uint8_t* __restrict__ inc, const float* __restrict__ ec, int W,
                                        int Wc, int y, int x, float om, float sc, float mu) {
   const int a = y * W + x;
-  float z = om * invd[a] * (b[a] - mu);
-  if (inc[a]) z += sc * ec[(y >> 1) * Wc + (x >> 1)];
-  return z;
+  const float bb = b[a], id = invd[a], e = ec[(y >> 1) * Wc + (x >> 1)];
+  const bool ic = inc[a] != 0;
+  return om * id * (bb - mu) + (ic ? sc * e : 0.f);
+}
+
+// Restriction of the 2x2 block (cy, cx) of a level: the sum over its aggregated
+// cells of the residual after one damped Jacobi step from zero,
+// (b_a - mu) - sum_n w_an (y_a - y_n), y = om D^-1 (b - mu).  Every load of the
+// 4x4 window (b, 1/d), the 2x3 right and 3x2 down weights and the flags is
+// issued before any arithmetic (one round trip instead of a chain); terms of
+// absent edges are selected away, so unwritten values never propagate.
+__device__ __forceinline__ float restrict_block(const float* __restrict__ b, const float* __restrict__ invd,
+                                                const float* __restrict__ wr, const float* __restrict__ wd,
+                                                const uint8_t* __restrict__ inc, int H, int W, int cy, int cx,
+                                                float om, float mu) {
+  const int y0 = 2 * cy, x0 = 2 * cx;
+  float yv[4][4], bv[2][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      yv[i][j] = 0.f;
+      if ((i == 0 || i == 3) && (j == 0 || j == 3)) continue;
+      const int y = y0 - 1 + i, x = x0 - 1 + j;
+      const bool in = y >= 0 && y < H && x >= 0 && x < W;
+      const int a = in ? y * W + x : 0;
+      const float bb = in ? b[a] : 0.f, id = in ? invd[a] : 0.f;
+      yv[i][j] = om * id * (bb - mu);
+      if (i >= 1 && i <= 2 && j >= 1 && j <= 2) bv[i - 1][j - 1] = bb - mu;
+    }
+  float wrv[2][3], wdv[3][2];
+  bool incv[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int y = y0 + i, x = x0 - 1 + j;
+      wrv[i][j] = (y < H && x >= 0 && x < W) ? wr[y * W + x] : 0.f;
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int y = y0 - 1 + i, x = x0 + j;
+      wdv[i][j] = (y >= 0 && y < H && x < W) ? wd[y * W + x] : 0.f;
+    }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int y = y0 + i, x = x0 + j;
+      incv[i][j] = (y < H && x < W) ? inc[y * W + x] != 0 : false;
+    }
+  float s = 0.f;
+#pragma unroll
+  for (int di = 0; di < 2; ++di)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      const int i = di + 1, j = dj + 1;
+      const float ya = yv[i][j];
+      const float wR = wrv[di][dj + 1], wL = wrv[di][dj], wD = wdv[di + 1][dj], wU = wdv[di][dj];
+      float t = 0.f;
+      t += wR != 0.f ? wR * (ya - yv[i][j + 1]) : 0.f;
+      t += wL != 0.f ? wL * (ya - yv[i][j - 1]) : 0.f;
+      t += wD != 0.f ? wD * (ya - yv[i + 1][j]) : 0.f;
+      t += wU != 0.f ? wU * (ya - yv[i - 1][j]) : 0.f;
+      s += incv[di][dj] ? bv[di][dj] - t : 0.f;
+    }
+  return s;
 }
 
 // restriction of level f (>= 1) to level c over cells i0, i0 + stride, ...
@@ -157,42 +199,50 @@ __device__ void mg_down(const Lv& f, const Lv& c, float om, int i0, int stride, 
   for (int I = i0; I < nc; I += stride) {
     const int cy = I / c.W, cx = I - cy * c.W;
     const int lc = c.lab[I];
-    float s = 0.f;
-    if (lc >= 0 && (act == nullptr || act[lc])) {
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) {
-          const int fy = 2 * cy + dy, fx = 2 * cx + dx;
-          if (fy < f.H && fx < f.W && f.inc[fy * f.W + fx])
-            s += res_jac(f.b, f.invd, f.wr, f.wd, f.H, f.W, fy, fx, om, 0.f);
-        }
-    }
-    c.b[I] = s;
+    const float s = restrict_block(f.b, f.invd, f.wr, f.wd, f.inc, f.H, f.W, cy, cx, om, 0.f);
+    const bool on = lc >= 0 && (act == nullptr || act[lc]);
+    c.b[I] = on ? s : 0.f;
   }
+}
+
+// prolongation and post-smoothing of cell (y, x) of level f: with
+// zc = om D^-1 b + sc P e_c, e_f = zc + om D^-1 (b - A zc); all loads first
+__device__ __forceinline__ float prolong_cell(const float* __restrict__ b, const float* __restrict__ invd,
+                                              const float* __restrict__ wr, const float* __restrict__ wd,
+                                              const uint8_t* __restrict__ inc, const float* __restrict__ ec,
+                                              int H, int W, int Wc, int y, int x, float om, float sc,
+                                              float mu) {
+  const int dy[5] = {0, 0, 0, -1, 1}, dx[5] = {0, 1, -1, 0, 0};
+  float zc[5], ba = 0.f, ida = 0.f;
+#pragma unroll
+  for (int n = 0; n < 5; ++n) {
+    const int yy = y + dy[n], xx = x + dx[n];
+    const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+    const int a = in ? yy * W + xx : 0;
+    const float bb = in ? b[a] - mu : 0.f, id = in ? invd[a] : 0.f;
+    const bool ic = in && inc[a] != 0;
+    const float e = in ? ec[(yy >> 1) * Wc + (xx >> 1)] : 0.f;
+    zc[n] = om * id * bb + (ic ? sc * e : 0.f);
+    if (n == 0) { ba = bb; ida = id; }
+  }
+  const int a = y * W + x;
+  const float w0 = wr[a], w1 = x > 0 ? wr[a - 1] : 0.f, w2 = wd[a], w3 = y > 0 ? wd[a - W] : 0.f;
+  float t = 0.f;
+  t += w0 != 0.f ? w0 * (zc[0] - zc[1]) : 0.f;
+  t += w1 != 0.f ? w1 * (zc[0] - zc[2]) : 0.f;
+  t += w3 != 0.f ? w3 * (zc[0] - zc[3]) : 0.f;
+  t += w2 != 0.f ? w2 * (zc[0] - zc[4]) : 0.f;
+  return zc[0] + om * ida * (ba - t);
 }
 
 // prolongation and post-smoothing on level f (>= 1): e_f from b_f and e_c
 __device__ void mg_up(const Lv& f, const Lv& c, float om, float sc, int i0, int stride) {
   const int n = f.H * f.W;
   for (int a = i0; a < n; a += stride) {
-    if (f.lab[a] < 0) { f.e[a] = 0.f; continue; }
     const int y = a / f.W, x = a - y * f.W;
-    const float za = zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x, om, sc, 0.f);
-    float s = 0.f;
-    const float w0 = f.wr[a];
-    if (w0 != 0.f) s += w0 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x + 1, om, sc, 0.f));
-    if (x > 0) {
-      const float w1 = f.wr[a - 1];
-      if (w1 != 0.f) s += w1 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y, x - 1, om, sc, 0.f));
-    }
-    const float w2 = f.wd[a];
-    if (w2 != 0.f) s += w2 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y + 1, x, om, sc, 0.f));
-    if (y > 0) {
-      const float w3 = f.wd[a - f.W];
-      if (w3 != 0.f) s += w3 * (za - zc_at(f.b, f.invd, f.inc, c.e, f.W, c.W, y - 1, x, om, sc, 0.f));
-    }
-    f.e[a] = za + om * f.invd[a] * (f.b[a] - s);
+    const int la = f.lab[a];
+    const float e = prolong_cell(f.b, f.invd, f.wr, f.wd, f.inc, c.e, f.H, f.W, c.W, y, x, om, sc, 0.f);
+    f.e[a] = la >= 0 ? e : 0.f;
   }
 }
 
@@ -280,19 +330,10 @@ __device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k) {
   if (cy >= H1 || cx >= W1) return;
   const int I = cy * W1 + cx;
   const int lc = A.clab[A.loff[1] + I];
-  float s = 0.f;
-  if (lc >= 0 && (!CHECK || comp_now(A, lc, k))) {
-    const float mu = comp_mean(A, lc, k);
-#pragma unroll
-    for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const int fy = 2 * cy + dy, fx = 2 * cx + dx;
-        if (fy < A.H && fx < A.W && A.inc0[fy * A.W + fx])
-          s += res_jac(A.r, A.invd, A.wr, A.wd, A.H, A.W, fy, fx, A.om, mu);
-      }
-  }
-  A.cb[A.loff[1] + I] = s;
+  const float mu = (A.project && lc >= 0) ? comp_mean(A, lc, k) : 0.f;
+  const float s = restrict_block(A.r, A.invd, A.wr, A.wd, A.inc0, A.H, A.W, cy, cx, A.om, mu);
+  const bool on = lc >= 0 && (!CHECK || comp_now(A, lc, k));
+  A.cb[A.loff[1] + I] = on ? s : 0.f;
 }
 
 template <bool ALIGNED>
@@ -520,8 +561,11 @@ __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   float ec[4];
   {
     const float* er = e1 + (size_t)(g.row >> 1) * W1;
+    float e0 = 0.f, e2 = 0.f;
+    if (g.nval > 0) e0 = er[g.col >> 1];
+    if (g.nval > 2) e2 = er[(g.col + 2) >> 1];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ec[j] = (j < g.nval && u4get(in4, j)) ? er[(g.col + j) >> 1] : 0.f;
+    for (int j = 0; j < 4; ++j) ec[j] = (j < g.nval && u4get(in4, j)) ? (j < 2 ? e0 : e2) : 0.f;
   }
   float4 zc;
 #pragma unroll
@@ -529,32 +573,39 @@ __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   float zl = __shfl_up_sync(NI_FULL, zc.w, 1), zr = __shfl_down_sync(NI_FULL, zc.x, 1);
   float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
   if (l8 == 0) {
-    wl0 = (g.nval > 0 && g.col > 0) ? A.wr[g.a - 1] : 0.f;
-    zl = wl0 != 0.f ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc, mu[0]) : 0.f;
+    const bool ok = g.nval > 0 && g.col > 0;
+    wl0 = ok ? A.wr[g.a - 1] : 0.f;
+    const float zz = ok ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col - 1, om, sc, mu[0]) : 0.f;
+    zl = wl0 != 0.f ? zz : 0.f;
   }
-  if (l8 == 7)
-    zr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f)
-             ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc, mu[3])
-             : 0.f;
+  if (l8 == 7) {
+    const bool ok = g.nval == 4 && g.col + 4 < W;
+    const float zz = ok ? zc_at(A.r, A.invd, A.inc0, e1, W, W1, g.row, g.col + 4, om, sc, mu[3]) : 0.f;
+    zr = (ok && wr4.w != 0.f) ? zz : 0.f;
+  }
   float4 zu = make_float4(0, 0, 0, 0), zd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
   if (g.row > 0) {
     wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
     const float4 ru = ldg<ALIGNED>(A.r, g.a - W, g.nval), iu = ldg<ALIGNED>(A.invd, g.a - W, g.nval);
     const uchar4 cu = ldinc<ALIGNED>(A.inc0, g.a - W, g.nval);
     const float* er = e1 + (size_t)((g.row - 1) >> 1) * W1;
+    const float e0 = g.nval > 0 ? er[g.col >> 1] : 0.f, e2 = g.nval > 2 ? er[(g.col + 2) >> 1] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < g.nval && f4get(wu4, j) != 0.f)
-        f4set(zu, j, om * f4get(iu, j) * (f4get(ru, j) - mu[j]) + (u4get(cu, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+    for (int j = 0; j < 4; ++j) {
+      const float zz = om * f4get(iu, j) * (f4get(ru, j) - mu[j]) + (u4get(cu, j) ? sc * (j < 2 ? e0 : e2) : 0.f);
+      f4set(zu, j, (j < g.nval && f4get(wu4, j) != 0.f) ? zz : 0.f);
+    }
   }
   if (g.row + 1 < H) {
     const float4 rd = ldg<ALIGNED>(A.r, g.a + W, g.nval), idd = ldg<ALIGNED>(A.invd, g.a + W, g.nval);
     const uchar4 cd = ldinc<ALIGNED>(A.inc0, g.a + W, g.nval);
     const float* er = e1 + (size_t)((g.row + 1) >> 1) * W1;
+    const float e0 = g.nval > 0 ? er[g.col >> 1] : 0.f, e2 = g.nval > 2 ? er[(g.col + 2) >> 1] : 0.f;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < g.nval && f4get(wd4, j) != 0.f)
-        f4set(zd, j, om * f4get(idd, j) * (f4get(rd, j) - mu[j]) + (u4get(cd, j) ? sc * er[(g.col + j) >> 1] : 0.f));
+    for (int j = 0; j < 4; ++j) {
+      const float zz = om * f4get(idd, j) * (f4get(rd, j) - mu[j]) + (u4get(cd, j) ? sc * (j < 2 ? e0 : e2) : 0.f);
+      f4set(zd, j, (j < g.nval && f4get(wd4, j) != 0.f) ? zz : 0.f);
+    }
   }
   float4 z4;
   float pv[1][4];
@@ -599,16 +650,32 @@ __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   };
   const float4 z4 = ldg<ALIGNED>(A.z, g.a, g.nval), po4 = ldg<ALIGNED>(pold, g.a, g.nval);
   const float4 wr4 = ldg<ALIGNED>(A.wr, g.a, g.nval), wd4 = ldg<ALIGNED>(A.wd, g.a, g.nval);
-  int sl[4];
-  tile_slots(ul, lab, sl, S.lab);
-  if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) S.f[threadIdx.x * 4] = betaf(S.lab[threadIdx.x]);
-  __syncthreads();
+  // row ends: the neighbours' z, p and weight, loaded with the rest
+  const bool okl = l8 == 0 && g.nval > 0 && g.col > 0, okr = l8 == 7 && g.nval == 4 && g.col + 4 < W;
+  const float wle = okl ? A.wr[g.a - 1] : 0.f;
+  const float zle = okl ? A.z[g.a - 1] : 0.f, ple = okl ? pold[g.a - 1] : 0.f;
+  const float zre = okr ? A.z[g.a + 4] : 0.f, pre = okr ? pold[g.a + 4] : 0.f;
   float beta[4];
   bool now[4];
+  if (ul >= 0) {   // one component: lane 0 of each warp computes beta, no CTA barrier
+    float bt = (threadIdx.x & 31) == 0 ? betaf(ul) : 0.f;
+    bt = __shfl_sync(NI_FULL, bt, 0);
+    const bool on = actk[ul] != 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    now[j] = lab[j] >= 0 && actk[lab[j]];
-    beta[j] = sl[j] >= 0 ? S.f[sl[j] * 4] : (sl[j] == -2 ? betaf(lab[j]) : 0.f);
+    for (int j = 0; j < 4; ++j) {
+      now[j] = lab[j] >= 0 && on;
+      beta[j] = bt;
+    }
+  } else {
+    int sl[4];
+    tile_slots(ul, lab, sl, S.lab);
+    if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) S.f[threadIdx.x * 4] = betaf(S.lab[threadIdx.x]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      now[j] = lab[j] >= 0 && actk[lab[j]];
+      beta[j] = sl[j] >= 0 ? S.f[sl[j] * 4] : (sl[j] == -2 ? betaf(lab[j]) : 0.f);
+    }
   }
   float4 pn;
 #pragma unroll
@@ -616,14 +683,10 @@ __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   float pl = __shfl_up_sync(NI_FULL, pn.w, 1), pr = __shfl_down_sync(NI_FULL, pn.x, 1);
   float wl0 = __shfl_up_sync(NI_FULL, wr4.w, 1);
   if (l8 == 0) {
-    const int a = g.a - 1;
-    wl0 = (g.nval > 0 && g.col > 0) ? A.wr[a] : 0.f;
-    pl = (wl0 != 0.f && now[0]) ? A.z[a] + beta[0] * pold[a] : 0.f;
+    wl0 = wle;
+    pl = (wl0 != 0.f && now[0]) ? zle + beta[0] * ple : 0.f;
   }
-  if (l8 == 7) {
-    const int a = g.a + 4;
-    pr = (g.nval == 4 && g.col + 4 < W && wr4.w != 0.f && now[3]) ? A.z[a] + beta[3] * pold[a] : 0.f;
-  }
+  if (l8 == 7) pr = (okr && wr4.w != 0.f && now[3]) ? zre + beta[3] * pre : 0.f;
   float4 pu = make_float4(0, 0, 0, 0), pd = make_float4(0, 0, 0, 0), wu4 = make_float4(0, 0, 0, 0);
   if (g.row > 0) {
     wu4 = ldg<ALIGNED>(A.wd, g.a - W, g.nval);
@@ -677,13 +740,23 @@ __device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   };
   float4 x4 = ldg<ALIGNED>(A.x, g.a, g.nval), r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
   const float4 p4 = ldg<ALIGNED>(pnew, g.a, g.nval), q4 = ldg<ALIGNED>(A.q, g.a, g.nval);
-  int sl[4];
-  tile_slots(ul, lab, sl, S.lab);
-  if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) {
-    S.f[threadIdx.x * 4] = alphaf(S.lab[threadIdx.x]);
-    S.f[threadIdx.x * 4 + 1] = comp_mean(A, S.lab[threadIdx.x], k);
+  int sl[4] = {-1, -1, -1, -1};
+  float ual = 0.f, umu = 0.f;
+  if (ul >= 0) {   // one component: lane 0 of each warp computes the scalars
+    if ((threadIdx.x & 31) == 0) {
+      ual = alphaf(ul);
+      umu = comp_mean(A, ul, k);
+    }
+    ual = __shfl_sync(NI_FULL, ual, 0);
+    umu = __shfl_sync(NI_FULL, umu, 0);
+  } else {
+    tile_slots(ul, lab, sl, S.lab);
+    if (threadIdx.x < TAB_SLOTS && S.lab[threadIdx.x] >= 0) {
+      S.f[threadIdx.x * 4] = alphaf(S.lab[threadIdx.x]);
+      S.f[threadIdx.x * 4 + 1] = comp_mean(A, S.lab[threadIdx.x], k);
+    }
+    __syncthreads();
   }
-  __syncthreads();
   float pv[2][4];
   bool now[4];
 #pragma unroll
@@ -691,7 +764,10 @@ __device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
     now[j] = lab[j] >= 0 && actk[lab[j]];
     float al = 0.f, mu = 0.f;
     if (now[j]) {
-      if (sl[j] >= 0) {
+      if (ul >= 0) {
+        al = ual;
+        mu = umu;
+      } else if (sl[j] >= 0) {
         al = S.f[sl[j] * 4];
         mu = S.f[sl[j] * 4 + 1];
       } else if (sl[j] == -2) {
