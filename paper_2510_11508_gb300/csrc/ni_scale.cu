@@ -174,20 +174,44 @@ __global__ void k_radix_hist(const unsigned long long* __restrict__ keys, const 
   for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * gridDim.x + blockIdx.x] = hcount[d];
 }
 
-// single-block exclusive scan of n <= 1024 * 64 ints in place
+// single-block exclusive scan of n <= 1024 * 64 ints in place: each warp owns a
+// contiguous segment and walks it 32 elements at a time (coalesced), a block
+// scan of the warp totals gives the segment offsets
 __global__ void k_scan_big(int* __restrict__ a, int n, const int* gate) {
-  __shared__ int sh[40];
+  __shared__ int wsum[32];
   if (gated(gate)) return;
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
-  int s = 0;
-  for (int i = beg; i < end; ++i) s += a[i];
-  int tot;
-  int ex = block_excl_scan_i(s, sh, &tot);
-  for (int i = beg; i < end; ++i) {
-    int v = a[i];
-    a[i] = ex;
-    ex += v;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int seg = (n + nw - 1) / nw;
+  const int beg = min(n, warp * seg), end = min(n, beg + seg);
+  int tot = 0;
+#pragma unroll 8
+  for (int i = beg + lane; i < end; i += 32) tot += a[i];
+  tot = warp_sum_i(tot);
+  if (lane == 0) wsum[warp] = tot;
+  __syncthreads();
+  if (warp == 0) {
+    const int v = lane < nw ? wsum[lane] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(NI_FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nw) wsum[lane] = x - v;
+  }
+  __syncthreads();
+  int run = wsum[warp];
+  for (int i0 = beg; i0 < end; i0 += 32) {
+    const int i = i0 + lane;
+    const int v = i < end ? a[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(NI_FULL, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < end) a[i] = run + x - v;
+    run += __shfl_sync(NI_FULL, x, 31);
   }
 }
 
