@@ -591,18 +591,23 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   bool done = !(gg > 0.0) || gg <= stop2;
   // q = L p with a group of G lanes per row: the quotient graph's degrees follow
   // the component sizes (a large component borders thousands of small ones), so
-  // the multi-CTA path gives each row a warp; one CTA (K <= 1024) a thread
-  const int G = gridDim.x == 1 ? 1 : 32;
-  const int lane = threadIdx.x & (G - 1), gw = tid / G, nw = nthr / G;
+  // the multi-CTA path gives each row a warp, one CTA a thread or four lanes
+  const int G = gridDim.x > 1 ? 32 : (K <= 1024 ? 1 : 4);
+  const int lane32 = threadIdx.x & 31, lane = lane32 & (G - 1), rpw = 32 / G;   // rows per warp pass
+  const int wid = tid >> 5, nwarp = nthr >> 5;
   while (!done && it < A.maxit) {
     double pq = 0, d1 = 0, d2 = 0;
-    for (int c = gw; c < K; c += nw) {
-      const double pc = A.pp[c];
+    // trip counts are uniform across a warp, so the group reductions can shuffle
+    for (int base = wid * rpw; base < K; base += nwarp * rpw) {
+      const int c = base + lane32 / G;
+      const bool valid = c < K;
+      const double pc = valid ? A.pp[c] : 0.0;
       double acc = 0.0;
-      for (int j = A.row_ptr[c] + lane; j < A.row_ptr[c + 1]; j += G)
-        acc += A.p_acc[3 * A.csr_pair[j]] * (pc - A.pp[A.csr_col[j]]);
-      if (G > 1) acc = warp_sum_d(acc);
-      if (lane == 0) {
+      if (valid)
+        for (int j = A.row_ptr[c] + lane; j < A.row_ptr[c + 1]; j += G)
+          acc += A.p_acc[3 * A.csr_pair[j]] * (pc - A.pp[A.csr_col[j]]);
+      for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(NI_FULL, acc, o);
+      if (valid && lane == 0) {
         A.qq[c] = acc;
         pq += pc * acc;
       }
@@ -654,10 +659,10 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   }
 }
 
-// one CTA up to 1024 components (at most 32 rows per warp, no grid barrier);
-// above, about 8 rows per warp
+// one CTA (no grid barrier) up to 8192 components: a thread per row up to 1024,
+// four lanes per row above; beyond, about 8 rows per warp over several CTAs
 int scale_cg_grid(ni_handle* h) {
-  if (h->Kcap <= 1024) return 1;
+  if (h->Kcap <= 8192) return 1;
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scale_cg, 1024, 0);
   int g = h->num_sms * std::max(1, std::min(per_sm, 2));

@@ -66,3 +66,17 @@ def test_depth_loss_is_blind_to_per_component_offsets():
     tz2 = tz + np.where(tl >= 0, 5.0 * (tl + 1), 0.0)
     l1 = CO.loss_and_grad_out(out, tz2, tl, tw, 0.0)[0]
     assert abs(l0 - l1) < 1e-9 * max(1, l0)
+
+
+def test_committed_network_file_layout():
+    """The trained warm-start network shipped with the package: magic, parameter
+    count of the architecture, tile size, finite weights."""
+    import os
+    import struct
+    path = os.path.join(os.path.dirname(__file__), "..", "paper_2510_11508_gb300", "nets", "warmstart_256.bin")
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"NICNN001"
+    n, tile = struct.unpack("<ii", raw[8:16])
+    assert n == CO.num_params() and tile == 256
+    w = np.frombuffer(raw[16:], np.float32)
+    assert w.size == n and np.isfinite(w).all()

@@ -106,11 +106,8 @@ def test_pipeline_runs_full_size(name, warm, tmp_path):
     H, W = w.mask.shape
     n, m = dev(w.normals, w.mask)
     it = integrator(H, W, w.camera, w.params, warm_start=warm)
-    if warm:
-        net = cnn.Net(16, 256, seed=3)
-        path = str(tmp_path / "net.bin")
-        net.save(path)
-        it.load_net(path)
+    if warm:   # the network trained on 10k maps of the C2 generator at 256 x 256
+        it.load_net(os.path.join(os.path.dirname(cnn.__file__), "nets", "warmstart_256.bin"))
     depth, labels, st = it.integrate(n, m)
     d = depth.cpu().numpy()
     it.close()
