@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--precond", type=int, default=1, help="batched fill: 0 Jacobi, 1 multigrid")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
+    ap.add_argument("--pixel-level", action="store_true",
+                    help="theta_c = None: every pixel its own component (the paper's pixel-level setting)")
     return ap.parse_args()
 
 
@@ -170,6 +172,8 @@ def run_ours(args):
     w = make_workload(args.config)
     H, W = w.mask.shape
     params = dict(w.params)
+    if args.pixel_level:
+        params["theta_c_deg"] = None
     cfg = ni.config_for(H, W, w.camera, params, batched=1 if args.variant == "batched" else 0,
                         precision=args.precision, precond=args.precond)
     it = ni.Integrator(cfg)

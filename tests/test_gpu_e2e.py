@@ -76,3 +76,32 @@ def test_full_size_c3(precond):
     assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
     np.testing.assert_array_equal(labels, ref["labels"])
     assert err <= 1e-4
+
+
+@pytest.mark.parametrize("name", ["c1", "c2"])
+def test_pixel_level_limit_matches_oracle(name):
+    """theta_c = None: every pixel is its own component (the paper's pixel-level
+    setting); the relative-scale loop then works on the pixel graph itself."""
+    w, depth, labels, st, ref = _run(name, theta_c_deg=None)
+    zg = np.log(depth) if w.camera["camera"] == 1 else depth
+    err = rel_depth_error(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, w.camera["camera"])
+    print(name, "pixel level", {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges", "ms_scale")},
+          "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
+    assert st["K0"] == int(w.mask.sum()) == ref["K0"]
+    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
+    np.testing.assert_array_equal(labels, ref["labels"])
+    assert err <= 1e-4
+
+
+@pytest.mark.parametrize("over", [dict(hard_outliers=True), dict(L=1e-6), dict(L=1e-4, U=1e-2)],
+                         ids=["hard", "L1e-6", "L1e-4_U1e-2"])
+def test_outlier_variants_match_oracle(over):
+    """The outlier reweighting variants of the supplementary ablation: the hard
+    threshold and other (L, U) of Eq. 11."""
+    w, depth, labels, st, ref = _run("c3_small", **over)
+    err = rel_depth_error(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
+    print(over, {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges")}, "oracle", ref["K"], ref["iters"],
+          "err", err)
+    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
+    np.testing.assert_array_equal(labels, ref["labels"])
+    assert err <= 1e-4
