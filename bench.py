@@ -4,11 +4,11 @@
 One step = one pass of the whole hot path (seeding, fill, relative-scale loop
 with merging, output) over one synthetic normal map through ni_integrate.
 Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-(the reference arm of this build) on a bounded sample of the same workload.
+(the reference arm) on a bounded sample of the same workload.
 
-Multi-GPU: replicas only (each rank integrates its own copy of the map; the
-method has no exchange step on one map in this build), value = all ranks'
-valid pixels / max-over-ranks time.
+Multi-GPU: replicas only (each rank integrates its own copy of the map; one
+map's path has no exchange step here), value = all ranks' valid pixels /
+max-over-ranks time.
 """
 from __future__ import annotations
 

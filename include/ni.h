@@ -207,7 +207,7 @@ ni_status ni_integrate_host(ni_handle* h, const float* normals_host, const uint8
  * invalid pixels.  NI_ERR_STATE before ni_solve_components. */
 ni_status ni_get_logdepth(ni_handle* h, float* logdepth_out, ni_stream_t stream);
 
-/* Learned warm start (not in the paper; an extension of the build): load the
+/* Learned warm start (not in the paper; an extension beyond it): load the
  * 6-layer 3x3 conv net's weights from a file written by the training code.
  * NI_ERR_INVALID_ARG if the file is missing or malformed. */
 ni_status ni_load_net(ni_handle* h, const char* path);

@@ -1,7 +1,7 @@
 /*
  * ni_cnn.h - C ABI of the learned warm start of libni.
  *
- * Not part of the paper (an extension of this build; the paper names learned
+ * Not part of the paper (an extension beyond it; the paper names learned
  * component heuristics only as future work in its conclusions).  A 6-layer
  * 3x3 convolutional network, 32 channels, ReLU after layers 1-5:
  *   input  4 channels per pixel: (n_x, n_y, n_z, mask)

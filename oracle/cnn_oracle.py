@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of the learned warm-start network (an extension of this build,
+"""FP64 CPU oracle of the learned warm-start network (an extension beyond the paper,
 not a method of the paper).  TEST INFRASTRUCTURE ONLY.
 
 Network: 6 valid 3x3 convolutions, channels 4 -> 32 -> 32 -> 32 -> 32 -> 32 -> 5,

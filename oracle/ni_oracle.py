@@ -582,7 +582,7 @@ def integrate(normals, mask, cam, params, record=False):
 
 
 # ---------------------------------------------------------------------------
-# evaluation helpers (alignment of Sec. 4; readings documented in the design doc)
+# evaluation helpers (alignment of Sec. 4: each island of the mask up to its own scale or offset)
 # ---------------------------------------------------------------------------
 
 def islands(mask):

@@ -1,4 +1,4 @@
-// Learned warm start (not in the paper; an extension of this build): a 6-layer
+// Learned warm start (not in the paper; an extension beyond it): a 6-layer
 // 3x3 convolutional network trained and run with BF16 tensor-core kernels.
 //
 // Convolutions are implicit GEMMs on mma.sync.m16n8k16 (BF16 inputs, FP32

@@ -58,7 +58,7 @@ __device__ __forceinline__ void ldlab(const int* l, int a, int nval, int (&lab)[
 #define TAB_SLOTS 64
 
 // Two-sum of float pairs (Knuth): hi + lo carries ~48 bits, the "compensated
-// FP32" reduction of the build (no FP64 instructions per pixel).
+// FP32" reduction (no FP64 instructions per pixel).
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
   const float s = hi + h2;
   const float bp = s - hi;

@@ -1,7 +1,7 @@
 """Component fill (Sec. 3.3, Eqs. 9-10): the GPU's per-component log-depth
 against the oracle's minimum-norm least-squares solution.
 
-Tolerance: the build's accuracy bound is a relative depth RMSE of 1e-4 for the
+Tolerance: the accuracy bound is a relative depth RMSE of 1e-4 for the
 FP64-reduction path and 1e-3 for the reduced-precision path; an error dz in
 log-depth is a relative depth error of dz, so the same numbers bound the RMS of
 the log-depth difference (orthographic: relative to the depth range)."""
