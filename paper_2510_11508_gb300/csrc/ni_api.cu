@@ -108,7 +108,7 @@ static void release_components(ni_handle* h) {
 static void release_edges(ni_handle* h) {
   dfree(h->e_id); dfree(h->e_id2); dfree(h->e_key); dfree(h->e_key2); dfree(h->e_val);
   dfree(h->e_val2); dfree(h->e_pair); dfree(h->p_lo); dfree(h->p_hi); dfree(h->p_acc);
-  dfree(h->c_key); dfree(h->c_val); dfree(h->csr_col); dfree(h->csr_pair);
+  dfree(h->c_key); dfree(h->c_val); dfree(h->csr_col); dfree(h->csr_pair); dfree(h->csr_w);
   h->Ecap = 0;
 }
 
@@ -159,6 +159,7 @@ ni_status ensure_edge_capacity(ni_handle* h, int nE) {
   if (e == cudaSuccess) e = dalloc(&h->c_val, 2 * n);
   if (e == cudaSuccess) e = dalloc(&h->csr_col, 2 * n);
   if (e == cudaSuccess) e = dalloc(&h->csr_pair, 2 * n);
+  if (e == cudaSuccess) e = dalloc(&h->csr_w, 2 * n);
   if (e != cudaSuccess) {
     release_edges(h);
     return ni_cuda_check(h, e, "edge buffers");

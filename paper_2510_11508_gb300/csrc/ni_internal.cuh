@@ -139,6 +139,7 @@ struct ni_handle {
   int* c_val = nullptr;
   int* csr_col = nullptr;      // [2 * Ecap]
   int* csr_pair = nullptr;     // [2 * Ecap]
+  double* csr_w = nullptr;     // [2 * Ecap] pair weight of each CSR entry (per scale iteration)
   int* radix_hist = nullptr;   // [256 * NI_SORT_BLOCKS]
 
   // multigrid hierarchy of the fill (precond = 1): coarse levels 1..mg_L in pools

@@ -481,7 +481,7 @@ __global__ void k_edge_accum(EdgeArgs A) {
 __global__ void k_node_assemble(const int* __restrict__ row_ptr, const int* __restrict__ csr_pair,
                                 const int* __restrict__ p_lo, const double* __restrict__ p_acc,
                                 DevState* st, double* __restrict__ diag, double* __restrict__ g,
-                                double* __restrict__ gabs) {
+                                double* __restrict__ gabs, double* __restrict__ csr_w) {
   if (st->converged) return;
   const int K = st->K;
   const int lane = threadIdx.x & 31;
@@ -490,7 +490,9 @@ __global__ void k_node_assemble(const int* __restrict__ row_ptr, const int* __re
     double d = 0.0, gs = 0.0, ga = 0.0;
     for (int j = row_ptr[c] + lane; j < row_ptr[c + 1]; j += 32) {
       int p = csr_pair[j];
-      d += p_acc[3 * p];
+      const double wp = p_acc[3 * p];
+      csr_w[j] = wp;   // the entry's weight for the SpMVs of this iteration
+      d += wp;
       const double hp = p_acc[3 * p + 1];
       gs += (p_lo[p] == c) ? -hp : hp;
       ga += fabs(hp);
@@ -510,6 +512,7 @@ struct ScaleArgs {
   DevState* st;
   const int* row_ptr;
   const int* csr_col;
+  const double* csr_w;
   const int* csr_pair;
   const int* p_lo;
   const int* p_hi;
@@ -592,22 +595,30 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   // q = L p with a group of G lanes per row: the quotient graph's degrees follow
   // the component sizes (a large component borders thousands of small ones), so
   // the multi-CTA path gives each row a warp, one CTA a thread or four lanes
-  const int G = gridDim.x > 1 ? 32 : (K <= 1024 ? 1 : 4);
-  const int lane32 = threadIdx.x & 31, lane = lane32 & (G - 1), rpw = 32 / G;   // rows per warp pass
-  const int wid = tid >> 5, nwarp = nthr >> 5;
+  // q = L p.  Rows of at most 32 entries take a thread each, longer rows a warp
+  // each: the quotient graph's degrees follow the component sizes (a large
+  // component borders thousands of small ones).  Entry weights come from csr_w.
+  const int lane = threadIdx.x & 31, wid = tid >> 5, nwarp = nthr >> 5;
   while (!done && it < A.maxit) {
     double pq = 0, d1 = 0, d2 = 0;
-    // trip counts are uniform across a warp, so the group reductions can shuffle
-    for (int base = wid * rpw; base < K; base += nwarp * rpw) {
-      const int c = base + lane32 / G;
-      const bool valid = c < K;
-      const double pc = valid ? A.pp[c] : 0.0;
+    for (int c = tid; c < K; c += nthr) {
+      const int b = A.row_ptr[c], e = A.row_ptr[c + 1];
+      if (e - b > 32) continue;
+      const double pc = A.pp[c];
       double acc = 0.0;
-      if (valid)
-        for (int j = A.row_ptr[c] + lane; j < A.row_ptr[c + 1]; j += G)
-          acc += A.p_acc[3 * A.csr_pair[j]] * (pc - A.pp[A.csr_col[j]]);
-      for (int o = G >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(NI_FULL, acc, o);
-      if (valid && lane == 0) {
+#pragma unroll 4
+      for (int j = b; j < e; ++j) acc += A.csr_w[j] * (pc - A.pp[A.csr_col[j]]);
+      A.qq[c] = acc;
+      pq += pc * acc;
+    }
+    for (int c = wid; c < K; c += nwarp) {   // warp-uniform
+      const int b = A.row_ptr[c], e = A.row_ptr[c + 1];
+      if (e - b <= 32) continue;
+      const double pc = A.pp[c];
+      double acc = 0.0;
+      for (int j = b + lane; j < e; j += 32) acc += A.csr_w[j] * (pc - A.pp[A.csr_col[j]]);
+      acc = warp_sum_d(acc);
+      if (lane == 0) {
         A.qq[c] = acc;
         pq += pc * acc;
       }
@@ -659,8 +670,8 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   }
 }
 
-// one CTA (no grid barrier) up to 8192 components: a thread per row up to 1024,
-// four lanes per row above; beyond, about 8 rows per warp over several CTAs
+// one CTA (no grid barrier) up to 8192 components; beyond, about 8 rows per warp
+// over several CTAs
 int scale_cg_grid(ni_handle* h) {
   if (h->Kcap <= 8192) return 1;
   int per_sm = 0;
@@ -683,9 +694,9 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   k_edge_accum<<<ge, 256, 0, s>>>(ea); NI_COUNT(h);
   k_node_assemble<<<grid_lin(h, 32LL * h->Kcap), 256, 0, s>>>(h->row_ptr, h->csr_pair, h->p_lo, h->p_acc, st,
                                                         h->sd, h->sv + 5 * (size_t)h->Kcap,
-                                                        h->sv + 6 * (size_t)h->Kcap); NI_COUNT(h);
+                                                        h->sv + 6 * (size_t)h->Kcap, h->csr_w); NI_COUNT(h);
   ScaleArgs sa;
-  sa.st = st; sa.row_ptr = h->row_ptr; sa.csr_col = h->csr_col; sa.csr_pair = h->csr_pair;
+  sa.st = st; sa.row_ptr = h->row_ptr; sa.csr_col = h->csr_col; sa.csr_w = h->csr_w; sa.csr_pair = h->csr_pair;
   sa.p_lo = h->p_lo; sa.p_hi = h->p_hi; sa.p_acc = h->p_acc; sa.diag = h->sd;
   sa.g = h->sv + 5 * (size_t)h->Kcap;
   sa.gabs = h->sv + 6 * (size_t)h->Kcap;
