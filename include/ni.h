@@ -96,7 +96,7 @@ typedef struct {
   int mg_coarse_sweeps;     /* damped-Jacobi steps on the coarsest multigrid level (0: 4) */
   int precond;              /* preconditioner of the batched fill: 0 Jacobi, 1 (default) one
                                symmetric V-cycle of aggregation multigrid on the pixel grid */
-  double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.8) */
+  double mg_omega;          /* damped-Jacobi smoothing weight of the V-cycle (0: 0.9) */
   double mg_correction;     /* scale of the coarse-grid correction (0: 1) */
   int mg_cta_cells;         /* coarse-level cells per CTA of a restriction/prolongation pass; the
                                pass syncs only its CTAs (0: 256, one cell per thread) */
@@ -125,6 +125,8 @@ typedef struct {
   int64_t fill_px_iters;    /* sum over components of pixels x PCG iterations */
   int64_t kernel_launches;  /* kernels this call launched (graph nodes included) */
   int32_t warm_fallbacks;   /* components whose energy-optimal warm-start scale was 0 (cold start) */
+  int32_t fill_fallbacks;   /* components the multigrid PCG left above the tolerance after 2000
+                               iterations, finished by the Jacobi PCG */
 } ni_stats;
 
 /* Default configuration for an H x W map (Algorithm 1's defaults of the paper's

@@ -316,6 +316,7 @@ extern "C" ni_status ni_solve_components(ni_handle* h, float* logdepth_out, ni_s
     return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
   cudaStream_t s = (cudaStream_t)stream;
   h->err.clear();
+  h->fill_fallbacks = 0;
   ni_status rc = fill_setup_launch(h, s);
   if (rc != NI_OK) return rc;
   cudaMemsetAsync(h->x, 0, sizeof(float) * h->N, s);
@@ -496,6 +497,7 @@ extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint
     stats->fill_px_iters = (int64_t)d->fill_px_iters;
     stats->kernel_launches = h->launches - launches0;
     stats->warm_fallbacks = d->warm_fallbacks;
+    stats->fill_fallbacks = h->fill_fallbacks;
   }
   if (fill_rc != NI_OK) return ni_fail(h, fill_rc, fill_msg);
   return NI_OK;

@@ -848,7 +848,12 @@ static void* pcg_fn() {
   return (void*)k_pcg_tiles<FP64, AL>;
 }
 
-static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
+__global__ void k_clear_fill_flags(DevState* st) {
+  st->fill_unconv = 0;
+  st->err &= ~NI_DEV_ERR_FILL_NOCONV;
+}
+
+static ni_status batched_solve(ni_handle* h, cudaStream_t s, bool allow_warm = true) {
   const bool f64 = h->cfg.precision == 0;
   const bool al = (h->W % 4) == 0;
   void* fn = f64 ? (al ? pcg_fn<true, true>() : pcg_fn<true, false>())
@@ -870,7 +875,7 @@ static ni_status batched_solve(ni_handle* h, cudaStream_t s) {
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   a.maxit = h->cfg.cg_maxit; a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
-  a.warm = h->cfg.warm_start ? 1 : 0;
+  a.warm = (allow_warm && h->cfg.warm_start) ? 1 : 0;
   void* args[] = {&a};
   cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NI_TILE_THREADS), args, 0, s);
   NI_COUNT(h);
@@ -891,8 +896,22 @@ ni_status fill_solve_launch(ni_handle* h, cudaStream_t s) {
     cudaMemsetAsync(&h->st->fill_iters, 0, 2 * sizeof(int), s);
     cudaMemsetAsync(&h->st->fill_px_iters, 0, sizeof(unsigned long long), s);
     cudaEventRecord(h->ev[5], s);
-    if (h->cfg.batched) {
-      rc = h->cfg.precond == 1 ? mg_solve_launch(h, s) : batched_solve(h, s);
+    if (h->cfg.batched && h->cfg.precond == 1) {
+      rc = mg_solve_launch(h, s);
+      if (rc == NI_OK) {
+        // components the multigrid PCG left above the tolerance (float32 can stall
+        // it on rare components): Jacobi PCG continues them from where they are
+        cudaMemcpyAsync(&h->st_host->fill_unconv, &h->st->fill_unconv, sizeof(int), cudaMemcpyDeviceToHost, s);
+        rc = ni_cuda_check(h, cudaStreamSynchronize(s), "multigrid PCG");
+        if (rc == NI_OK && h->st_host->fill_unconv > 0) {
+          h->fill_fallbacks += h->st_host->fill_unconv;
+          k_clear_fill_flags<<<1, 1, 0, s>>>(h->st); NI_COUNT(h);
+          rc = batched_solve(h, s, false);
+        }
+      }
+      cudaEventRecord(h->ev[6], s);
+    } else if (h->cfg.batched) {
+      rc = batched_solve(h, s);
       cudaEventRecord(h->ev[6], s);
     } else {
       rc = plain_solve(h, s);

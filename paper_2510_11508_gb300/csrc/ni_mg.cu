@@ -16,7 +16,7 @@
 //     over the fine edges between two aggregates and the diagonal d_I = the
 //     weights of all edges leaving the aggregate plus its cells' own diagonal
 //     excess (sums of non-negative terms only);
-//   * smoothing: one damped Jacobi step (weight om, default 0.8) before and
+//   * smoothing: one damped Jacobi step (weight om, default 0.9) before and
 //     after the coarse correction, the coarse correction scaled by sc (default
 //     1; over-correction sc > 1 cut the iterations on some maps but left single
 //     components converging at a crawl in float32 on others); the coarsest level
@@ -99,6 +99,7 @@ __device__ __forceinline__ Lv coarse_level(const MgArgs& A, int l) {
 }
 
 #define MG_SMEM_CELLS 512
+#define NI_MG_MAXIT 2000
 
 // the small levels, held in shared memory by CTA 0
 struct MgSmem {
@@ -1280,10 +1281,12 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   cudaMemsetAsync(h->mg_bar, 0, sizeof(GridBar) * 2 * (NI_MG_MAX_LEVELS + 1), s);
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
-  a.maxit = h->cfg.cg_maxit; a.warm = h->cfg.warm_start ? 1 : 0;
+  // the multigrid PCG converges in tens to hundreds of iterations; a component
+  // still above the tolerance after NI_MG_MAXIT goes to the Jacobi fallback
+  a.maxit = std::min(h->cfg.cg_maxit, NI_MG_MAXIT); a.warm = h->cfg.warm_start ? 1 : 0;
   a.ncs = h->cfg.mg_coarse_sweeps > 0 ? h->cfg.mg_coarse_sweeps : 4;
   a.project = (h->cfg.mg_flags & 1) ? 1 : 0;
-  a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.8f;
+  a.om = h->cfg.mg_omega > 0 ? (float)h->cfg.mg_omega : 0.9f;
   a.sc = h->cfg.mg_correction > 0 ? (float)h->cfg.mg_correction : 1.0f;
   a.tol2 = h->cfg.cg_rtol * h->cfg.cg_rtol;
   if (h->cfg.fill_kernels == 0) {

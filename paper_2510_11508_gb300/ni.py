@@ -52,7 +52,7 @@ class Stats(C.Structure):
                 ("fill_iters", C.c_int32), ("fill_unconverged", C.c_int32),
                 ("scale_cg_iters", C.c_int32), ("n_energy", C.c_int32), ("energy", C.c_double * 64),
                 ("ms_fill_solve", C.c_double), ("fill_px_iters", C.c_int64), ("kernel_launches", C.c_int64),
-                ("warm_fallbacks", C.c_int32)]
+                ("warm_fallbacks", C.c_int32), ("fill_fallbacks", C.c_int32)]
 
     def as_dict(self) -> Dict[str, object]:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "energy"}
