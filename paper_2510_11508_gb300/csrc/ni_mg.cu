@@ -833,6 +833,17 @@ __device__ void mg_epi_apply(const MgArgs& A, int i0, int stride) {
 // ---------------------------------------------------------------------------
 // persistent variant: one cooperative launch, grid barriers between phases
 // ---------------------------------------------------------------------------
+// the CTA's tiles of the list; the next entry is loaded before the current tile
+// is processed, so its latency hides behind the tile's work
+#define MG_TILE_LOOP(BODY)                                                       \
+  {                                                                              \
+    int2 nx = blockIdx.x < nt ? A.tiles[blockIdx.x] : make_int2(0, -2);          \
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {                           \
+      const int2 te = nx;                                                        \
+      if (i + (int)gridDim.x < nt) nx = A.tiles[i + gridDim.x];                  \
+      BODY;                                                                      \
+    }                                                                            \
+  }
 template <bool COMP, bool ALIGNED>
 __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   __shared__ TileSmem S;
@@ -861,7 +872,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   for (int k = 0;; ++k) {
     const int P = k & 1, Q = P ^ 1;
     comp_book(A, k, gtid, gthr);
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_down0(A, A.tiles[i].x, A.tiles[i].y, k);
+    MG_TILE_LOOP(tile_down0(A, te.x, te.y, k));
     if (!grid_barrier(&A.st->bar, err)) return;
     if (*(volatile int*)&A.ntl[2 + P] == 0) break;
     const int* actk = A.ci + (size_t)P * A.Kc;
@@ -882,12 +893,12 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       slot(A, MG_RR + Q)[c] = 0.0;
       slot(A, MG_SR + Q)[c] = 0.0;
     }
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_up0<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
+    MG_TILE_LOOP((tile_up0<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_dir<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
+    MG_TILE_LOOP((tile_dir<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
     for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_upd<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y, k, actk);
+    MG_TILE_LOOP((tile_upd<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
   }
   for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_epi_sums(A, S, A.tiles[i].x, A.tiles[i].y);
