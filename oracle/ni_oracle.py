@@ -290,8 +290,8 @@ def solve_min_norm(M, g):
     """Minimum-norm solution of the singular normal equations M x = g of a
     weighted graph Laplacian M (the result cg(M, g) approaches from x = 0).
 
-    Written out as its definition: on each connected block of M's graph
-    (off-diagonal entries != 0) one node is pinned to 0, the remaining
+    Written out as its definition, block by block: on each connected block of
+    M's graph (off-diagonal entries != 0) one node is pinned to 0, the remaining
     nonsingular system is solved by sparse LU (scipy's spsolve), and the block's
     mean is removed (the null space of a connected Laplacian block is the
     constants).  Isolated nodes get 0.  Returns x."""
@@ -303,16 +303,24 @@ def solve_min_norm(M, g):
     off = M - sp.diags(M.diagonal())
     off.eliminate_zeros()
     nb, blk = connected_components(off, directed=False)
-    first = np.full(nb, n, np.int64)
-    np.minimum.at(first, blk, np.arange(n))
-    keep = np.ones(n, bool)
-    keep[first] = False
+    g = np.asarray(g, np.float64)
+    # blocks made contiguous: the blocks of P M P^T are its diagonal blocks
+    order = np.argsort(blk, kind="stable")
+    bounds = np.searchsorted(blk[order], np.arange(nb + 1))
+    Mp = M[order][:, order].tocsr()
+    gp = g[order]
+    xp = np.zeros(n)
+    for c in range(nb):
+        b0, b1 = bounds[c], bounds[c + 1]
+        if b1 - b0 < 2:
+            continue
+        # pin the block's first node (its smallest index) to 0
+        Mk = Mp[b0 + 1:b1, b0 + 1:b1].tocsc()
+        # symmetric minimum-degree ordering: the fill-in of a grid Laplacian
+        # stays near-linear, so components of 1e6 pixels fit in host memory
+        xp[b0 + 1:b1] = spsolve(Mk, gp[b0 + 1:b1], permc_spec="MMD_AT_PLUS_A")
     x = np.zeros(n)
-    if keep.any():
-        # symmetric minimum-degree ordering of M + M^T: the fill-in of a grid
-        # Laplacian stays near-linear, so maps of 1e7 pixels fit in host memory
-        Mk = M[keep][:, keep].tocsc()
-        x[keep] = spsolve(Mk, np.asarray(g)[keep], permc_spec="MMD_AT_PLUS_A")
+    x[order] = xp
     return project_zero_mean(x, blk, nb)
 
 

@@ -30,7 +30,7 @@ from . import ni
 SPACE = {
     "ctas_per_sm": [2, 4],
     "mg_cta_cells": [128, 256, 512],
-    "mg_omega": [0.67, 0.8, 0.9],
+    "mg_omega": [0.8, 0.9, 0.95],
     "mg_correction": [1.0],
 }
 
