@@ -9,8 +9,8 @@ Always run (the oracle computes these in well under a minute):
     only its own pixels, so the crop's answer is the full map's answer; the
     crop keeps the rays by shifting the principal point);
   * the whole pipeline runs, with the stop test, merges and output contract.
-With NI_FULL_SIZE=1: Algorithm 1 end to end against the oracle (minutes of
-CPU time and tens of GB of host memory)."""
+The oracle's end-to-end run does not fit these maps: the largest components
+(millions of pixels) exceed the host sparse LU's limits."""
 import os
 
 import numpy as np
@@ -121,21 +121,3 @@ def test_pipeline_runs_full_size(name, warm, tmp_path):
     assert st["K_final"] <= st["K0"]
     if w.params["can_merge"] and st["scale_iters"] >= w.params["freq_merging"] + 1:
         assert st["merges"] >= 1
-
-
-@pytest.mark.skipif(not os.environ.get("NI_FULL_SIZE"), reason="set NI_FULL_SIZE=1 (minutes of oracle time)")
-@pytest.mark.parametrize("name", ["c4_eval", "c5"])
-def test_full_oracle_parity_full_size(name):
-    w = _workload(name)
-    H, W = w.mask.shape
-    n, m = dev(w.normals, w.mask)
-    it = integrator(H, W, w.camera, w.params)
-    depth, labels, st = it.integrate(n, m)
-    ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(w.params))
-    err = rel_depth_error(np.nan_to_num(np.log(depth.cpu().numpy())), np.nan_to_num(ref["z"]), w.mask, 1)
-    print(name, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "ms_total")},
-          "oracle", ref["K0"], ref["K"], ref["iters"], "rel depth RMSE", err)
-    assert st["K0"] == ref["K0"]
-    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
-    np.testing.assert_array_equal(labels.cpu().numpy(), ref["labels"])
-    assert err <= 1e-4
