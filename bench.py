@@ -128,6 +128,27 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (the slowest replica sets the job's time);
+    x itself without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(seconds: float, units_per_rank: int, steps: int) -> float:
+    """Whole-job Mpixel/s of N replicas: all ranks' units over the max-over-ranks
+    time (weak scaling: every rank integrates its own map)."""
+    import torch.distributed as dist
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    return units_per_rank * steps * world / seconds / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -231,12 +252,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = n_valid * args.steps * world / (ms / 1e3) / 1e6
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = replica_throughput(ms / 1e3, n_valid, args.steps)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     nh = torch.from_numpy(w.normals).pin_memory()
@@ -250,12 +267,8 @@ def run_ours(args):
     for _ in range(args.steps):
         it.integrate_host(nh, mh, out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": n_valid * args.steps * world / e2e_s / 1e6, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": replica_throughput(e2e_s, n_valid, args.steps), "unit": UNIT,
            "h2d_bytes_per_step": int(nh.numel() * 4 + mh.numel()),
            "d2h_bytes_per_step": int(out.numel() * 4)}
 
