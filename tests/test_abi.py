@@ -71,3 +71,27 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "oracle" not in txt.replace("oracles", ""), f
+
+
+@pytest.mark.parametrize("field,value", [
+    ("H", 0), ("connectivity", 8), ("T", 0), ("T", 1000), ("precision", 2), ("precond", 2),
+    ("mg_omega", 1.0), ("mg_correction", 4.0), ("ctas_per_sm", 9), ("fill_kernels", 2),
+    ("mg_coarse_sweeps", 100), ("cg_maxit", 0), ("n_fill_irls", 0), ("dE_max", -1.0),
+])
+def test_invalid_config_rejected_before_any_device_call(lib, field, value):
+    """ni_create validates the whole config on the host and returns
+    NI_ERR_INVALID_ARG (no device is touched, so this runs without a GPU)."""
+    from paper_2510_11508_gb300 import ni
+    cfg = ni.default_config(64, 64)
+    setattr(cfg, field, type(getattr(cfg, field))(value))
+    h = C.c_void_p()
+    assert lib.ni_create(C.byref(cfg), C.byref(h)) == 1   # NI_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_warm_start_needs_the_batched_fill(lib):
+    from paper_2510_11508_gb300 import ni
+    cfg = ni.default_config(64, 64)
+    cfg.warm_start, cfg.batched = 1, 0
+    h = C.c_void_p()
+    assert lib.ni_create(C.byref(cfg), C.byref(h)) == 1
