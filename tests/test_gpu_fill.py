@@ -145,3 +145,14 @@ def test_multigrid_knobs_converge(om):
     assert st["fill_unconverged"] == 0
     if om == 0.9:
         assert st["fill_fallbacks"] == 0 and st["fill_iters"] < 400
+
+
+@pytest.mark.parametrize("name", ["c2", "c3_small"])
+def test_multigrid_mean_projection_option(name):
+    """mg_flags bit 0 (the residual's component mean projected out before each
+    V-cycle): same answer as the oracle."""
+    w = make_workload(name)
+    z, zr, K = _fill_pair(w.normals, w.mask, w.camera, w.params, batched=1, precond=1, mg_flags=1)
+    d = (z - zr)[w.mask > 0]
+    scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[w.mask > 0]))
+    assert float(np.sqrt(np.mean(d * d))) / scale <= 1e-4
