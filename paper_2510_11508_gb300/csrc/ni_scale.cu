@@ -517,7 +517,7 @@ struct ScaleArgs {
   const int* p_lo;
   const int* p_hi;
   const double* p_acc;
-  const double* diag;
+  double* diag;        // the Jacobi diagonal; replaced by its inverse at the start of the solve
   const double* g;
   const double* gabs;
   double* s;
@@ -533,12 +533,50 @@ struct ScaleArgs {
   double dE_max;
 };
 
+// CTA sum of three values, the same additions as three block_sum_d calls.  A
+// warp whose values are all zero (its rows lie past the last component) or sit
+// in lane 0 alone (a long row's result) skips its shuffle trees, which are most
+// of the FP64 instructions of an iteration when K is small against the CTA.
+__device__ __forceinline__ void block_sum3_d(double& a, double& b, double& c, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const unsigned m = __ballot_sync(NI_FULL, a != 0.0 || b != 0.0 || c != 0.0);
+  if (m & ~1u) {
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    c = warp_sum_d(c);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    sh[3 * wid] = a;
+    sh[3 * wid + 1] = b;
+    sh[3 * wid + 2] = c;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    double x = lane < nw ? sh[3 * lane] : 0.0, y = lane < nw ? sh[3 * lane + 1] : 0.0,
+           z = lane < nw ? sh[3 * lane + 2] : 0.0;
+    x = warp_sum_d(x);
+    y = warp_sum_d(y);
+    z = warp_sum_d(z);
+    if (lane == 0) {
+      sh[96] = x;
+      sh[97] = y;
+      sh[98] = z;
+    }
+  }
+  __syncthreads();
+  a = sh[96];
+  b = sh[97];
+  c = sh[98];
+}
+
 // Grid-wide sum of three values.  gridDim 1: a block reduction.  Otherwise
 // partial sums go to rotating slots (slot m % 3 at call m; block 0 clears slot
 // (m + 1) % 3, last read two calls ago) followed by a bounded grid barrier.
 __device__ __forceinline__ bool grid_sum3(double& a, double& b, double& c, double* red, int& ncall,
                                           DevState* st, double* sh) {
-  double ba = block_sum_d(a, sh), bb = block_sum_d(b, sh), bc = block_sum_d(c, sh);
+  double ba = a, bb = b, bc = c;
+  block_sum3_d(ba, bb, bc, sh);
   if (gridDim.x == 1) {
     a = ba; b = bb; c = bc;
     return true;
@@ -566,7 +604,7 @@ __device__ __forceinline__ bool gsync(DevState* st) {
 }
 
 __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
-  __shared__ double sh[33];
+  __shared__ double sh[99];
   DevState* st = A.st;
   if (*(volatile int*)&st->converged) return;
   const int K = st->K, P = st->nP;
@@ -575,7 +613,9 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   double rz = 0, ga2 = 0, gg = 0;
   for (int c = tid; c < K; c += nthr) {
     const double d = A.diag[c], rc = A.g[c];
-    const double zc = d > 0.0 ? rc / d : 0.0;
+    const double id = d > 0.0 ? 1.0 / d : 0.0;   // one FP64 division per component and solve
+    A.diag[c] = id;
+    const double zc = rc * id;
     A.s[c] = 0.0;
     A.r[c] = rc;
     A.z[c] = zc;
@@ -592,9 +632,6 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
   const double stop2 = fmax(A.tol2 * gg, floor2);
   int it = 0;
   bool done = !(gg > 0.0) || gg <= stop2;
-  // q = L p with a group of G lanes per row: the quotient graph's degrees follow
-  // the component sizes (a large component borders thousands of small ones), so
-  // the multi-CTA path gives each row a warp, one CTA a thread or four lanes
   // q = L p.  Rows of at most 32 entries take a thread each, longer rows a warp
   // each: the quotient graph's degrees follow the component sizes (a large
   // component borders thousands of small ones).  Entry weights come from csr_w.
@@ -616,6 +653,7 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
       if (e - b <= 32) continue;
       const double pc = A.pp[c];
       double acc = 0.0;
+#pragma unroll 4
       for (int j = b + lane; j < e; j += 32) acc += A.csr_w[j] * (pc - A.pp[A.csr_col[j]]);
       acc = warp_sum_d(acc);
       if (lane == 0) {
@@ -630,8 +668,7 @@ __global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
       A.s[c] += alpha * A.pp[c];
       const double rc = A.r[c] - alpha * A.qq[c];
       A.r[c] = rc;
-      const double d = A.diag[c];
-      const double zc = d > 0.0 ? rc / d : 0.0;
+      const double zc = rc * A.diag[c];
       A.z[c] = zc;
       rzn += rc * zc;
       rrn += rc * rc;
