@@ -626,3 +626,70 @@ def aligned_rel_rmse(z, z_ref, mask, camera):
     if camera == PERSP:
         return float(err / np.sqrt(np.mean(zr[m] ** 2)))
     return float(err / max(np.ptp(zr[m]), 1e-300))
+
+
+def min_made(depth, depth_gt, labels, K, camera):
+    """Minimum theoretical mean absolute depth error of a decomposition
+    (supplementary material, the section on the components found for different
+    theta_c): the MADE the reconstruction would reach with the best scale of
+    each component, i.e. the per-component minimal MADEs weighted by their
+    pixel counts.
+
+    depth: [H, W] depth of the reconstruction (exp(z~) for the perspective
+    camera, z~ for the orthographic reading), depth_gt: [H, W], labels:
+    [H, W] component of each pixel (-1 excluded) or None for one component of
+    all pixels (then K = 1: the MADE after the best global scale).  A pixel
+    counts if its label is >= 0 and both depths are finite (and positive for
+    the perspective camera).
+
+    Reading: the paper gives no formula.  A component's scale multiplies its
+    depth for the perspective camera (it adds to the log-depth) and adds to the
+    depth for the orthographic reading, whose components are fixed up to an
+    offset.  Per component
+        E_c = min_s sum_{i in c} |s d_i - g_i|   (perspective)
+        E_c = min_s sum_{i in c} |d_i + s - g_i| (orthographic)
+    and MADE = sum_c E_c / sum_c n_c.  E_c is a convex piecewise-linear
+    function of s whose minimum lies where its slope changes sign: at a
+    median of r_i = g_i / d_i weighted by d_i (perspective: |s d - g| =
+    d |s - r|), or at a median of r_i = g_i - d_i (orthographic).
+
+    Returns (made, per-component MADE E_c / n_c [K] (0 if n_c = 0),
+    per-component minimiser s_c [K] (NaN if n_c = 0)); made is NaN when no
+    pixel counts.  Parity pinned by tests/test_made_pins.py (closed forms,
+    brute force over the breakpoints, invariance, coarsening)."""
+    d = np.asarray(depth, np.float64).reshape(-1)
+    g = np.asarray(depth_gt, np.float64).reshape(-1)
+    if labels is None:
+        lab = np.zeros(d.size, np.int64)
+        K = 1
+    else:
+        lab = np.asarray(labels).reshape(-1).astype(np.int64)
+    ok = (lab >= 0) & np.isfinite(d) & np.isfinite(g)
+    if camera == PERSP:
+        ok &= (d > 0) & (g > 0)
+    idx = np.nonzero(ok)[0]
+    idx = idx[np.argsort(lab[idx], kind="stable")]
+    bounds = np.searchsorted(lab[idx], np.arange(K + 1))
+    err = np.zeros(K)
+    cnt = np.zeros(K, np.int64)
+    scale = np.full(K, np.nan)
+    for c in range(K):
+        sel = idx[bounds[c]:bounds[c + 1]]
+        if sel.size == 0:
+            continue
+        dc, gc = d[sel], g[sel]
+        if camera == PERSP:
+            r, w = gc / dc, dc
+        else:
+            r, w = gc - dc, np.ones_like(dc)
+        o = np.argsort(r, kind="stable")
+        cw = np.cumsum(w[o])
+        s = r[o][np.searchsorted(cw, 0.5 * cw[-1], side="left")]
+        e = np.abs(s * dc - gc) if camera == PERSP else np.abs(dc + s - gc)
+        err[c] = e.sum()
+        cnt[c] = sel.size
+        scale[c] = s
+    n = int(cnt.sum())
+    made = float(err.sum() / n) if n > 0 else float("nan")
+    per = np.where(cnt > 0, err / np.maximum(cnt, 1), 0.0)
+    return made, per, scale
