@@ -209,6 +209,36 @@ ni_status ni_integrate_host(ni_handle* h, const float* normals_host, const uint8
  * invalid pixels.  NI_ERR_STATE before ni_solve_components. */
 ni_status ni_get_logdepth(ni_handle* h, float* logdepth_out, ni_stream_t stream);
 
+/* Quality diagnostic (supplementary material, the section on the components
+ * found for different theta_c): the minimum mean absolute depth error that one
+ * scale per component can reach against a ground-truth depth map,
+ *   E_c = min_s sum_{i in c} |s d_i - g_i|    (perspective camera)
+ *   E_c = min_s sum_{i in c} |d_i + s - g_i|  (orthographic camera)
+ *   *made_out = sum_c E_c / (number of counted pixels),
+ * i.e. the per-component minimal MADEs weighted by their pixel counts.  With
+ * labels = NULL all pixels form one component: the MADE after the best global
+ * scale (offset), the error report of a finished reconstruction.
+ *   z: device float[H][W]: log-depth if z_is_log (d = exp(z), perspective
+ *      only; the orthographic z is linear depth either way), else depth (the
+ *      output of ni_integrate);
+ *   labels: device int32[H][W] with values in [-1, K) (-1 = excluded), or NULL;
+ *   K: number of components (ignored, taken as 1, when labels is NULL);
+ *   depth_gt: device float[H][W] ground-truth depth;
+ *   made_out: host; NaN if no pixel counts;
+ *   comp_made_out: device double[K], E_c / n_c (0 for an empty component), may be NULL;
+ *   comp_scale_out: device double[K], a minimising s per component (NaN for an
+ *      empty one), may be NULL.
+ * A pixel counts if its label is >= 0 and d, g are finite (and positive for
+ * the perspective camera).  Computed in FP64 by bisection of each
+ * component's weighted median; the per-component error is exact up to the
+ * order of the FP64 sums.  NI_ERR_INVALID_ARG if K is outside [1, H * W] or
+ * a label is >= K (then nothing is written).  Independent of the stage calls;
+ * scratch (20 bytes per pixel, 60 per component) is owned by the handle from
+ * the first call on.  Synchronises `stream`. */
+ni_status ni_min_made(ni_handle* h, const float* z, int z_is_log, const int32_t* labels, int32_t K,
+                      const float* depth_gt, double* made_out, double* comp_made_out,
+                      double* comp_scale_out, ni_stream_t stream);
+
 /* Learned warm start (not in the paper; an extension beyond it): load the
  * 6-layer 3x3 conv net's weights from a file written by the training code.
  * NI_ERR_INVALID_ARG if the file is missing or malformed. */

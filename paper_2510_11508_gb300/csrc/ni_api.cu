@@ -242,6 +242,7 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   dfree(h->in_normals); dfree(h->in_mask); dfree(h->out_depth);
   dfree(h->tile_in); dfree(h->tile_out);
   free_mg(h);
+  free_made(h);
   if (h->net) ni_cnn_destroy(h->net);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (int i = 0; i < 8; ++i)

@@ -184,6 +184,9 @@ struct ni_handle {
   float* tile_in = nullptr;
   float* tile_out = nullptr;
 
+  // scratch of ni_min_made (allocated on first use)
+  struct MadeScratch* made = nullptr;
+
   // device copies for ni_integrate_host
   float4* in_normals = nullptr;
   uint8_t* in_mask = nullptr;
@@ -231,6 +234,9 @@ int scale_cg_grid(ni_handle* h);
 void merge_gate_launch(ni_handle* h, int tgate, int force, cudaStream_t s);
 ni_status ensure_edge_capacity(ni_handle* h, int nE);
 ni_status ensure_component_capacity(ni_handle* h, int K);
+
+// ni_made.cu
+void free_made(ni_handle* h);
 
 // ni_cnn.cu
 ni_status warm_start_launch(ni_handle* h, cudaStream_t s);

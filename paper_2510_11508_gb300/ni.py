@@ -23,7 +23,7 @@ STATUS = {0: "NI_OK", 1: "NI_ERR_INVALID_ARG", 2: "NI_ERR_CUDA", 3: "NI_ERR_OOM"
 EXPORTS = ["ni_config_default", "ni_create", "ni_destroy", "ni_seed_components",
            "ni_solve_components", "ni_solve_scales", "ni_merge", "ni_merge_residuals",
            "ni_integrate", "ni_integrate_host", "ni_get_logdepth", "ni_load_net", "ni_last_error",
-           "ni_status_string", "ni_seed_components_noalloc"]
+           "ni_status_string", "ni_seed_components_noalloc", "ni_min_made"]
 
 
 class Camera(C.Structure):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False):
     L.ni_seed_components_noalloc.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(Camera), C.c_double,
                                              vp, vp, vp]
     L.ni_load_net.argtypes = [vp, C.c_char_p]
+    L.ni_min_made.argtypes = [vp, vp, C.c_int, vp, C.c_int32, vp, C.POINTER(C.c_double), vp, vp, vp]
     L.ni_last_error.argtypes = [vp]
     L.ni_last_error.restype = C.c_char_p
     L.ni_status_string.argtypes = [C.c_int]
@@ -259,3 +260,28 @@ class Integrator:
 
     def load_net(self, path: str):
         self._raise(self.L.ni_load_net(self.h, path.encode()))
+
+    # -- quality diagnostic ----------------------------------------------------
+    def min_made(self, z: torch.Tensor, depth_gt: torch.Tensor, labels: Optional[torch.Tensor] = None,
+                 K: int = 1, z_is_log: bool = True, per_component: bool = False):
+        """ni_min_made: the minimum mean absolute depth error one scale per
+        component reaches against depth_gt (labels None: the MADE after the best
+        global scale).  Returns the MADE, or (MADE, per-component MADE [K],
+        per-component scale [K]) as float64 CUDA tensors if per_component."""
+        _check_dev(z, torch.float32, (self.H, self.W), "z")
+        _check_dev(depth_gt, torch.float32, (self.H, self.W), "depth_gt")
+        if labels is not None:
+            _check_dev(labels, torch.int32, (self.H, self.W), "labels")
+        else:
+            K = 1
+        made = C.c_double()
+        comp = scale = None
+        if per_component:
+            comp = torch.empty(K, dtype=torch.float64, device=z.device)
+            scale = torch.empty(K, dtype=torch.float64, device=z.device)
+        self._raise(self.L.ni_min_made(self.h, z.data_ptr(), int(bool(z_is_log)),
+                                       None if labels is None else labels.data_ptr(), K,
+                                       depth_gt.data_ptr(), C.byref(made),
+                                       None if comp is None else comp.data_ptr(),
+                                       None if scale is None else scale.data_ptr(), _stream()))
+        return (made.value, comp, scale) if per_component else made.value
