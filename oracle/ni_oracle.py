@@ -37,6 +37,11 @@ ORTHO = 0
 PERSP = 1
 RIGHT = 0
 DOWN = 1
+DOWN_RIGHT = 2
+DOWN_LEFT = 3
+# (du, dv) from a to b for each edge direction; 4-connectivity uses the first two
+STEP_U = np.array([1, 0, 1, -1], np.int64)
+STEP_V = np.array([0, 1, 1, 1], np.int64)
 
 
 @dataclasses.dataclass
@@ -68,6 +73,7 @@ class Params:
     freq_merging: int = 5
     n_fill_irls: int = 1
     hard_outliers: bool = False
+    connectivity: int = 4
 
     @staticmethod
     def from_dict(d):
@@ -98,24 +104,36 @@ def rays(H: int, W: int, cam: Camera) -> np.ndarray:
     return t.reshape(-1, 3)
 
 
-def edge_list(mask: np.ndarray):
-    """All edges of the pixel graph G_0 = (V, E) with 4-connectivity (Sec. 3.2):
-    pairs (a, b) of valid neighbouring pixels, b the right (dir 0) or lower
-    (dir 1) neighbour of a.  Edges are returned sorted by the edge id
-    2 * a + dir."""
+def edge_id(a, d, conn=4):
+    """Edge id: 2 * a + dir with 4-connectivity, 4 * a + dir with 8."""
+    return (2 if conn == 4 else 4) * np.asarray(a, np.int64) + np.asarray(d, np.int64)
+
+
+def edge_list(mask: np.ndarray, conn: int = 4):
+    """All edges of the pixel graph G_0 = (V, E) (Sec. 3.2): pairs (a, b) of
+    valid neighbouring pixels, b the right (dir 0) or lower (dir 1) neighbour
+    of a; with 8-connectivity (the setting of the paper's DiLiGenT experiments
+    and of its connectivity ablation) also the lower-right (dir 2) and
+    lower-left (dir 3) neighbour.  Edges are returned sorted by edge_id."""
+    if conn not in (4, 8):
+        raise ValueError("connectivity must be 4 or 8")
     H, W = mask.shape
     m = mask.reshape(-1).astype(bool)
     idx = np.arange(H * W, dtype=np.int64)
     u = idx % W
     v = idx // W
-    ra = idx[(u < W - 1) & m]
-    ra = ra[m[ra + 1]]
-    da = idx[(v < H - 1) & m]
-    da = da[m[da + W]]
-    a = np.concatenate([ra, da])
-    d = np.concatenate([np.zeros(len(ra), np.int64), np.ones(len(da), np.int64)])
-    b = np.where(d == RIGHT, a + 1, a + W)
-    order = np.argsort(2 * a + d, kind="stable")
+    parts_a, parts_d = [], []
+    for dr in range(2 if conn == 4 else 4):
+        du, dv = int(STEP_U[dr]), int(STEP_V[dr])
+        inside = (u + du >= 0) & (u + du < W) & (v + dv < H) & m
+        a_ = idx[inside]
+        a_ = a_[m[a_ + du + dv * W]]
+        parts_a.append(a_)
+        parts_d.append(np.full(len(a_), dr, np.int64))
+    a = np.concatenate(parts_a)
+    d = np.concatenate(parts_d)
+    b = a + STEP_U[d] + STEP_V[d] * W
+    order = np.argsort(edge_id(a, d, conn), kind="stable")
     return a[order], b[order], d[order]
 
 
@@ -137,7 +155,8 @@ def omega(normals, cam: Camera, H: int, W: int, a, b, d) -> np.ndarray:
     Orthographic (Reading: the paper treats central cameras only): the same
     tangent-plane construction with parallel rays in linear depth gives
     z_a - z_b = (n_ax/n_az + n_bx/n_bz) / 2 for b right of a, and the same with
-    n_y for b below a.
+    n_y for b below a; for b = a + (du, dv) on a diagonal, the sum of the two
+    (du = +1 or -1, dv = +1); with a and b swapped, the negative.
 
     Pinned: exact on planes (closed form) and O(h^2) on a sphere.
     """
@@ -155,19 +174,24 @@ def omega(normals, cam: Camera, H: int, W: int, a, b, d) -> np.ndarray:
         num = np.maximum(np.abs(na_tm * nb_tb), 1e-300)
         den = np.maximum(np.abs(na_ta * nb_tm), 1e-300)
         return np.log(num / den)
-    comp = np.where(d == RIGHT, 0, 1)
-    return 0.5 * (n[a, comp] / n[a, 2] + n[b, comp] / n[b, 2])
+    gx = n[a, 0] / n[a, 2] + n[b, 0] / n[b, 2]
+    gy = n[a, 1] / n[a, 2] + n[b, 1] / n[b, 2]
+    # b = a - step(d) (the reversed edge) flips the sign
+    sgn = np.sign(np.asarray(b, np.int64) - np.asarray(a, np.int64)).astype(np.float64)
+    return sgn * (0.5 * np.select([d == RIGHT, d == DOWN, d == DOWN_RIGHT], [gx, gy, gx + gy], gy - gx))
 
 
 def gamma(normals, cam: Camera, H: int, W: int, p, d) -> np.ndarray:
     """gamma_{.->p} = f * n_p . tau_p (Sec. 3.1, Eq. 6), the pixel factor of the
     BiNI weight.  Reading: f = f_x for horizontal edges and f_y for vertical
-    ones, as in Eq. 2; orthographic: f = 1, tau = (0, 0, 1), so gamma = n_pz."""
+    ones, as in Eq. 2, and sqrt(f_x f_y) for diagonal ones (the paper names a
+    single focal length); orthographic: f = 1, tau = (0, 0, 1), so gamma = n_pz."""
     n = _normals64(normals)
     tau = rays(H, W, cam)
     nt = np.sum(n[p] * tau[p], 1)
     if cam.camera == PERSP:
-        return np.where(d == RIGHT, cam.fx, cam.fy) * nt
+        f = np.select([d == RIGHT, d == DOWN], [cam.fx, cam.fy], math.sqrt(cam.fx * cam.fy))
+        return f * nt
     return nt
 
 
@@ -193,8 +217,8 @@ def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
     ob = a - step
     ua, va = a % W, a // W
     sgn = np.sign(step)
-    du = np.where(d == RIGHT, -sgn, 0)
-    dv = np.where(d == RIGHT, 0, -sgn)
+    du = -sgn * STEP_U[d]
+    dv = -sgn * STEP_V[d]
     uo, vo = ua + du, va + dv
     inside = (uo >= 0) & (uo < W) & (vo >= 0) & (vo < H)
     obc = np.where(inside, ob, 0)
@@ -260,12 +284,12 @@ def canonical_labels(n_nodes: int, nodes: np.ndarray, ea, eb):
     return rank[cc], int(ncc)
 
 
-def seed_components(normals, mask, theta_c_deg):
+def seed_components(normals, mask, theta_c_deg, conn=4):
     """Initial partition {C_c^(0)}: connected components of the subgraph of G_0
     that keeps the edges with theta_{a,b} < theta_c (Sec. 3.3).  Returns
     (labels int64 [H*W], -1 at invalid pixels; K)."""
     H, W = mask.shape
-    a, b, d = edge_list(mask)
+    a, b, d = edge_list(mask, conn)
     keep = seed_edge_keep(normals, a, b, theta_c_deg)
     valid_idx = np.nonzero(mask.reshape(-1))[0]
     lab, K = canonical_labels(H * W, valid_idx, a[keep], b[keep])
@@ -339,15 +363,16 @@ class Geometry:
     omega: np.ndarray    # w~_{b->a} per edge
     gam_ba: np.ndarray   # gamma_{b->a} = f n_a.tau_a per edge
     gam_ab: np.ndarray   # gamma_{a->b} = f n_b.tau_b per edge
+    conn: int = 4        # pixel connectivity (4 or 8)
 
 
-def geometry(normals, mask, cam: Camera) -> Geometry:
+def geometry(normals, mask, cam: Camera, conn: int = 4) -> Geometry:
     H, W = mask.shape
-    a, b, d = edge_list(mask)
+    a, b, d = edge_list(mask, conn)
     return Geometry(H, W, mask.reshape(-1).astype(bool), a, b, d,
                     omega(normals, cam, H, W, a, b, d),
                     gamma(normals, cam, H, W, a, d),
-                    gamma(normals, cam, H, W, b, d))
+                    gamma(normals, cam, H, W, b, d), conn)
 
 
 def intra_system(geo: Geometry, labels, zt, k):
@@ -478,13 +503,14 @@ def merge_labels(labels, K, geo: Geometry, e, chi_abs32):
     (iii) its connected components are the new partition.
 
     Reading (tie-break, left open): edges are compared by the float32 value of
-    |chi| (its bit pattern), then by the edge id 2 * a + dir.  New labels are the
+    |chi| (its bit pattern), then by the edge id (2 * a + dir with
+    4-connectivity, 4 * a + dir with 8).  New labels are the
     ranks of each group's smallest old label (so label order follows the old
     one).  `chi_abs32` is float32 |chi| per edge in `e`.
     Returns (new labels [H*W], K_new, selected edge id per old component or -1)."""
     chi_abs32 = np.asarray(chi_abs32, np.float32)
     bits = chi_abs32.view(np.uint32).astype(np.uint64)
-    eid = (2 * geo.a[e] + geo.d[e]).astype(np.uint64)
+    eid = edge_id(geo.a[e], geo.d[e], geo.conn).astype(np.uint64)
     key = (bits << np.uint64(32)) | eid
     best = np.full(K, np.iinfo(np.uint64).max, np.uint64)
     pa, pb = labels[geo.a[e]], labels[geo.b[e]]
@@ -493,9 +519,10 @@ def merge_labels(labels, K, geo: Geometry, e, chi_abs32):
     has = best != np.iinfo(np.uint64).max
     sel_eid = np.where(has, (best & np.uint64(0xFFFFFFFF)).astype(np.int64), -1)
     # endpoints of the selected edges
-    ea = sel_eid[has] // 2
-    ed = sel_eid[has] % 2
-    eb = np.where(ed == RIGHT, ea + 1, ea + geo.W)
+    per = 2 if geo.conn == 4 else 4
+    ea = sel_eid[has] // per
+    ed = sel_eid[has] % per
+    eb = ea + STEP_U[ed] + STEP_V[ed] * geo.W
     newlab, Kn = canonical_labels(K, np.arange(K), labels[ea], labels[eb])
     out = labels.copy()
     v = labels >= 0
@@ -578,8 +605,8 @@ def integrate(normals, mask, cam, params, record=False):
         params = Params.from_dict(params)
     mask = np.asarray(mask).astype(np.uint8)
     H, W = mask.shape
-    geo = geometry(normals, mask, cam)
-    labels, K = seed_components(normals, mask, params.theta_c_deg)
+    geo = geometry(normals, mask, cam, params.connectivity)
+    labels, K = seed_components(normals, mask, params.theta_c_deg, params.connectivity)
     zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls)
     r = scale_loop(geo, labels, K, zt, params, record)
     out = r["z"].reshape(H, W)
@@ -593,10 +620,10 @@ def integrate(normals, mask, cam, params, record=False):
 # evaluation helpers (alignment of Sec. 4: each island of the mask up to its own scale or offset)
 # ---------------------------------------------------------------------------
 
-def islands(mask):
-    """Connected components of the valid-pixel graph G_0 (4-connectivity)."""
+def islands(mask, conn=4):
+    """Connected components of the valid-pixel graph G_0."""
     H, W = mask.shape
-    a, b, _ = edge_list(mask)
+    a, b, _ = edge_list(mask, conn)
     vidx = np.nonzero(mask.reshape(-1))[0]
     lab, n = canonical_labels(H * W, vidx, a, b)
     out = np.full(H * W, -1, np.int64)
@@ -604,13 +631,13 @@ def islands(mask):
     return out.reshape(H, W), n
 
 
-def aligned_rel_rmse(z, z_ref, mask, camera):
+def aligned_rel_rmse(z, z_ref, mask, camera, conn=4):
     """Relative depth RMSE of `z` against `z_ref` after the alignment the
     comparison needs, island by island (each island of the mask is
     reconstructed up to its own scale/offset):
       perspective: scale s* = <z, z_ref>/<z, z> per island, error / RMS(z_ref);
       orthographic: offset o* = mean(z_ref - z) per island, error / (max - min)(z_ref)."""
-    isl, n = islands(mask)
+    isl, n = islands(mask, conn)
     m = isl >= 0
     z = np.asarray(z, np.float64)
     zr = np.asarray(z_ref, np.float64)
