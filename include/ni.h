@@ -69,7 +69,10 @@ typedef struct {
   ni_camera cam;
   double theta_c_deg;       /* seeding threshold theta_c (Sec. 3.3); < 0 = None (one
                                component per pixel, the paper's pixel-level limit) */
-  int connectivity;         /* 4 (the only supported value) */
+  int connectivity;         /* 4 (default) or 8: pixel graph of the seeding; the fill,
+                               scale loop and merging are built for 4 only (with 8,
+                               ni_solve_components and ni_integrate* return
+                               NI_ERR_INVALID_ARG) */
   double k;                 /* sigmoid sharpness of the BiNI weight (Sec. 3.1), default 2 */
   double L, U;              /* outlier thresholds of Eq. 11, default 1e-5, 1e-3 */
   int T;                    /* maximum relative-scale iterations, default 15 */
@@ -141,8 +144,8 @@ ni_status ni_create(const ni_config* cfg, ni_handle** out);
 /* Release the handle and every buffer and graph it owns.  NULL is accepted. */
 ni_status ni_destroy(ni_handle* h);
 
-/* Sec. 3.3 seeding (rows a1-a2): for each 4-neighbour edge (a, b) with both
- * pixels valid, keep it iff n_a . n_b > cos(theta_c) (the dot product of the
+/* Sec. 3.3 seeding (rows a1-a2): for each 4-neighbour edge (a, b) (with
+ * connectivity 8 also each diagonal edge) with both pixels valid, keep it iff n_a . n_b > cos(theta_c) (the dot product of the
  * float32 inputs evaluated in float64, x then y then z; theta_c in degrees,
  * cos(theta_c_deg * (pi / 180))).  The components of the kept edges are
  * labelled canonically: label = rank of the component's smallest raster index;

@@ -75,7 +75,7 @@ extern "C" void ni_config_default(ni_config* c, int H, int W) {
 static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->H < 1 || c->W < 1) { why = "H and W must be >= 1"; return NI_ERR_INVALID_ARG; }
   if ((long long)c->H * c->W >= (1LL << 30)) { why = "H * W must be < 2^30"; return NI_ERR_INVALID_ARG; }
-  if (c->connectivity != 4) { why = "only 4-connectivity is supported"; return NI_ERR_INVALID_ARG; }
+  if (c->connectivity != 4 && c->connectivity != 8) { why = "connectivity must be 4 or 8"; return NI_ERR_INVALID_ARG; }
   if (c->cam.camera != 0 && c->cam.camera != 1) { why = "camera must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->cam.camera == 1 && !(c->cam.fx > 0 && c->cam.fy > 0)) {
     why = "focal lengths must be > 0"; return NI_ERR_INVALID_ARG;
@@ -310,8 +310,17 @@ extern "C" ni_status ni_seed_components(ni_handle* h, const float* normals, cons
   return ni_cuda_check(h, cudaStreamSynchronize(s), "seeding");
 }
 
+// The fill, relative-scale loop and merging are built for 4-connectivity; with
+// 8-connectivity the handle seeds only.
+static ni_status need_conn4(ni_handle* h) {
+  if (h->cfg.connectivity == 4) return NI_OK;
+  return ni_fail(h, NI_ERR_INVALID_ARG, "8-connectivity covers the seeding only: the fill, scale loop and "
+                                        "merging need connectivity = 4");
+}
+
 extern "C" ni_status ni_solve_components(ni_handle* h, float* logdepth_out, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
+  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (h->stage < 1) return ni_fail(h, NI_ERR_STATE, "ni_solve_components before ni_seed_components");
   if (h->cfg.warm_start && !h->net)
     return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
@@ -454,6 +463,7 @@ extern "C" ni_status ni_merge_residuals(ni_handle* h, const float* chi_abs, int3
 extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint8_t* mask, float* depth_out,
                                   int32_t* labels_out, ni_stats* stats, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
+  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (!depth_out) return ni_fail(h, NI_ERR_INVALID_ARG, "depth_out is required");
   cudaStream_t s = (cudaStream_t)stream;
   const long long launches0 = h->launches;
@@ -507,6 +517,7 @@ extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint
 extern "C" ni_status ni_integrate_host(ni_handle* h, const float* normals_host, const uint8_t* mask_host,
                                        float* depth_host, ni_stats* stats, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
+  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (!normals_host || !mask_host || !depth_host) return ni_fail(h, NI_ERR_INVALID_ARG, "null host buffer");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)h->N;

@@ -1,6 +1,7 @@
 // Seeding of continuous components (Sec. 3.3, first paragraph; rows a1-a2).
 //
-// Edge predicate: an edge (a, b) of the 4-neighbour pixel graph is kept iff
+// Edge predicate: an edge (a, b) of the 4-neighbour pixel graph (with
+// 8-connectivity also the diagonal edges) is kept iff
 // both pixels are valid and n_a . n_b > cos(theta_c), the dot product of the
 // float32 inputs evaluated in float64 (products are exact, sums rounded in the
 // order x, y, z), so the decision is bit-identical to any IEEE-754 evaluation
@@ -12,6 +13,7 @@
 //                  tile's internal edges united with shared-memory atomics,
 //                  tile roots written to the global parent array;
 //   k_seed_border  the edges that cross tile borders, united in global memory;
+//   k_seed_diag    8-connectivity only: every diagonal edge, in global memory;
 //   k_compress     parent[i] <- root(i);
 //   k_count_roots / scan / k_rank_roots / k_gather_labels
 //                  canonical labels = rank of each root among all roots in
@@ -101,6 +103,21 @@ __global__ void k_seed_border(const float4* __restrict__ nrm, const uint8_t* __r
     }
     if (!mask[a] || !mask[b]) continue;
     if (seed_keep(ldg4(&nrm[a]), ldg4(&nrm[b]), cth)) uf_unite(parent, a, b);
+  }
+}
+
+// 8-connectivity: the two diagonal edges of each pixel, to the lower-right and
+// lower-left neighbour, united in global memory after the 4-connected phases.
+__global__ void k_seed_diag(const float4* __restrict__ nrm, const uint8_t* __restrict__ mask, int H, int W,
+                            double cth, int* __restrict__ parent) {
+  const long long n = (long long)(H - 1) * W;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)i, x = a % W;
+    if (!mask[a]) continue;
+    const float4 na = ldg4(&nrm[a]);
+    if (x + 1 < W && mask[a + W + 1] && seed_keep(na, ldg4(&nrm[a + W + 1]), cth)) uf_unite(parent, a, a + W + 1);
+    if (x >= 1 && mask[a + W - 1] && seed_keep(na, ldg4(&nrm[a + W - 1]), cth)) uf_unite(parent, a, a + W - 1);
   }
 }
 
@@ -194,6 +211,10 @@ ni_status seed_launch(ni_handle* h, cudaStream_t s) {
   long long nb = (long long)nbx * H + (long long)nby * W;
   k_seed_border<<<grid_for(h, nb, 256), 256, 0, s>>>(h->normals, h->mask, H, W, h->cos_theta, nbx, nby,
                                                        h->parent); NI_COUNT(h);
+  if (h->cfg.connectivity == 8 && H > 1) {
+    k_seed_diag<<<grid_for(h, (long long)(H - 1) * W, 256), 256, 0, s>>>(h->normals, h->mask, H, W, h->cos_theta,
+                                                                        h->parent); NI_COUNT(h);
+  }
   k_compress<<<grid_for(h, N, 256), 256, 0, s>>>(h->parent, N); NI_COUNT(h);
   k_count_roots<<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(h->parent, nullptr, N, h->blk); NI_COUNT(h);
   scan_blocks_launch(h->blk, NI_SCAN_BLOCKS, h->d_count, s); NI_COUNT(h);
