@@ -128,6 +128,17 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def mask_islands(mask):
+    """Islands of the mask (4-connected components of the valid pixels):
+    int32 [H, W] labels, -1 outside the mask, and their number.  Each island
+    of a map is reconstructed up to its own scale, so errors against the
+    ground truth are taken after the best scale of every island."""
+    import numpy as np
+    from scipy import ndimage
+    lab, n = ndimage.label(np.asarray(mask) > 0)
+    return (lab.astype(np.int32) - 1), int(n)
+
+
 def max_over_ranks(x: float) -> float:
     """The largest x over all ranks (the slowest replica sets the job's time);
     x itself without an initialised process group."""
@@ -218,6 +229,16 @@ def run_ours(args):
         check = {"rel_rmse_vs_oracle": err, "labels_bit_exact": lab_ok, "K0": st["K0"],
                  "K_final": st["K_final"], "oracle_K_final": ref["K"], "iters": st["scale_iters"],
                  "oracle_iters": ref["iters"], "tolerance": 1e-4 if args.precision == 0 else 1e-3}
+        # error against the synthetic ground truth: MADE after the best scale (offset) of each island
+        gt32 = np.ascontiguousarray(w.depth_gt, dtype=np.float32)
+        isl, n_isl = mask_islands(w.mask)
+        try:
+            check["made_vs_gt"] = it.min_made(depth, torch.from_numpy(gt32).cuda(), torch.from_numpy(isl).cuda(),
+                                              n_isl, z_is_log=False)
+        except ni.NIError as e:
+            check["made_vs_gt"] = None
+            check["made_error"] = str(e)
+        check["oracle_made_vs_gt"] = O.min_made(ref["depth"], gt32, isl, n_isl, w.camera["camera"])[0]
         cpu = {"value": n_valid / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the full {w.name} workload ({n_valid} valid px), one run, {dt:.1f} s"}
 

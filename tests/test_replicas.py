@@ -50,3 +50,18 @@ def test_single_process_without_group():
     import bench
     assert bench.max_over_ranks(1.5) == 1.5
     assert bench.replica_throughput(2.0, 4_000_000, 5) == pytest.approx(10.0)
+
+
+def test_mask_islands_match_the_oracle():
+    """The bench's island labels (error alignment against the ground truth) are
+    the oracle's islands of the mask, label for label."""
+    import numpy as np
+    import bench
+    import oracle as O
+    rng = np.random.default_rng(2)
+    for H, W in ((1, 1), (17, 23), (64, 50)):
+        mask = (rng.random((H, W)) > 0.45).astype(np.uint8)
+        lab, n = bench.mask_islands(mask)
+        ref, nr = O.islands(mask)
+        assert n == nr and lab.dtype == np.int32
+        np.testing.assert_array_equal(lab, ref)
