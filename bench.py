@@ -235,7 +235,7 @@ def run_ours(args):
         try:
             check["made_vs_gt"] = it.min_made(depth, torch.from_numpy(gt32).cuda(), torch.from_numpy(isl).cuda(),
                                               n_isl, z_is_log=False)
-        except ni.NIError as e:
+        except (ni.NIError, ValueError) as e:   # a diagnostic: report, do not stop the bench
             check["made_vs_gt"] = None
             check["made_error"] = str(e)
         check["oracle_made_vs_gt"] = O.min_made(ref["depth"], gt32, isl, n_isl, w.camera["camera"])[0]
