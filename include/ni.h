@@ -69,10 +69,10 @@ typedef struct {
   ni_camera cam;
   double theta_c_deg;       /* seeding threshold theta_c (Sec. 3.3); < 0 = None (one
                                component per pixel, the paper's pixel-level limit) */
-  int connectivity;         /* 4 (default) or 8: pixel graph of the seeding; the fill,
-                               scale loop and merging are built for 4 only (with 8,
-                               ni_solve_components and ni_integrate* return
-                               NI_ERR_INVALID_ARG) */
+  int connectivity;         /* 4 (default) or 8 (H * W < 2^29, batched = 0): pixel
+                               graph of every stage.  With 8, the stages after the
+                               seeding are not yet enabled: ni_solve_components and
+                               ni_integrate* return NI_ERR_INVALID_ARG */
   double k;                 /* sigmoid sharpness of the BiNI weight (Sec. 3.1), default 2 */
   double L, U;              /* outlier thresholds of Eq. 11, default 1e-5, 1e-3 */
   int T;                    /* maximum relative-scale iterations, default 15 */
@@ -178,7 +178,8 @@ ni_status ni_solve_scales(ni_handle* h, int max_iters, float* logdepth_inout,
 /* Sec. 3.5 merging (row a6), now: each component selects its incident
  * inter-component edge of smallest |chi| = |z~_a - z~_b - omega~_{b->a}| at
  * the current log-depth (float32 |chi|, ties broken by the smaller edge id
- * 2 * a + dir, dir 0 = right, 1 = down); the connected components of the
+ * 2 * a + dir, dir 0 = right, 1 = down; with connectivity 8 the id 4 * a + dir,
+ * dir 2 = lower-right, 3 = lower-left); the connected components of the
  * selected edges form the new partition, labelled by the rank of their
  * smallest old label.  The log-depth is unchanged.  labels_out (device
  * int32[H][W], may be NULL), K_out (host, may be NULL).  Synchronises. */
@@ -187,8 +188,9 @@ ni_status ni_merge(ni_handle* h, int32_t* labels_out, int32_t* K_out, ni_stream_
 /* The merge of ni_merge with caller-given residual magnitudes instead of the
  * handle's: chi_abs is device float[H][W][2] holding |chi| of the right
  * (index 0) and down (index 1) edge of each pixel (entries of edges that are
- * not inter-component are ignored).  Used to test the merge on identical
- * inputs. */
+ * not inter-component are ignored); with connectivity 8 float[H][W][4], adding
+ * the lower-right (2) and lower-left (3) edge.  Used to test the merge on
+ * identical inputs. */
 ni_status ni_merge_residuals(ni_handle* h, const float* chi_abs, int32_t* labels_out,
                              int32_t* K_out, ni_stream_t stream);
 

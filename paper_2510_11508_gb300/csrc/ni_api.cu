@@ -76,6 +76,12 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->H < 1 || c->W < 1) { why = "H and W must be >= 1"; return NI_ERR_INVALID_ARG; }
   if ((long long)c->H * c->W >= (1LL << 30)) { why = "H * W must be < 2^30"; return NI_ERR_INVALID_ARG; }
   if (c->connectivity != 4 && c->connectivity != 8) { why = "connectivity must be 4 or 8"; return NI_ERR_INVALID_ARG; }
+  if (c->connectivity == 8 && (long long)c->H * c->W >= (1LL << 29)) {
+    why = "8-connectivity needs H * W < 2^29 (edge ids 4 a + dir)"; return NI_ERR_INVALID_ARG;
+  }
+  if (c->connectivity == 8 && c->batched) {
+    why = "8-connectivity runs the plain fill PCG: set batched = 0"; return NI_ERR_INVALID_ARG;
+  }
   if (c->cam.camera != 0 && c->cam.camera != 1) { why = "camera must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->cam.camera == 1 && !(c->cam.fx > 0 && c->cam.fy > 0)) {
     why = "focal lengths must be > 0"; return NI_ERR_INVALID_ARG;
@@ -209,6 +215,13 @@ extern "C" ni_status ni_create(const ni_config* cfg, ni_handle** out) {
   if (e == cudaSuccess) e = dalloc(&h->p2, NP);
   if (e == cudaSuccess) e = dalloc(&h->q, NP);
   if (e == cudaSuccess) e = dalloc(&h->b, NP);
+  if (cfg->connectivity == 8) {
+    if (e == cudaSuccess) e = dalloc(&h->omega_d, N);
+    if (e == cudaSuccess) e = dalloc(&h->wdr, NP);
+    if (e == cudaSuccess) e = dalloc(&h->wdl, NP);
+    if (e == cudaSuccess) e = cudaMemset(h->wdr, 0, NP * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->wdl, 0, NP * sizeof(float));
+  }
   if (e == cudaSuccess) e = dalloc(&h->tile_lab, (size_t)h->ntiles);
   if (e == cudaSuccess) e = dalloc(&h->tiles, 4 * (size_t)h->ntiles);
   // padding pixels beyond N: label -1, weights and vectors 0 (never written later)
@@ -236,6 +249,7 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   release_components(h);
   release_edges(h);
   dfree(h->labels); dfree(h->parent); dfree(h->omega); dfree(h->ntau); dfree(h->wr); dfree(h->wd);
+  dfree(h->omega_d); dfree(h->wdr); dfree(h->wdl);
   dfree(h->tile_lab); dfree(h->tiles);
   dfree(h->invd); dfree(h->x); dfree(h->r); dfree(h->p); dfree(h->p2); dfree(h->q); dfree(h->b);
   dfree(h->blk); dfree(h->d_count); dfree(h->radix_hist); dfree(h->st);

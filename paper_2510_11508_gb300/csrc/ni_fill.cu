@@ -157,6 +157,112 @@ __global__ void k_fill_reweight(const float* __restrict__ ntau, const int* __res
   }
 }
 
+// 8-connectivity: omega~ (Eq. 3, the same midpoint form as the axis edges with
+// tau_b - tau_a = (du / f_x, dv / f_y, 0)) and the fill weight at z~ = 0 of the
+// lower-right (du, dv) = (1, 1) and lower-left (-1, 1) edge of every valid
+// pixel; gamma uses f = sqrt(f_x f_y) on diagonals.  Orthographic: the sum of
+// the two axis terms, signed by the step.
+__device__ __forceinline__ void diag_edge(const float4 na, const float4 nb, float A, float B, int du, int persp,
+                                          float fx, float fy, float& om, float& w2) {
+  if (persp) {
+    const float da = du * na.x / fx + na.y / fy, db = du * nb.x / fx + nb.y / fy;
+    const float qv = (da * B + A * db) / (A * (2.f * B - db));
+    om = (qv > -1.f) ? log1pf(qv) : logf(fabsf(1.f + qv));
+    w2 = 0.5f * (fx * fy) * (A * A + B * B);
+  } else {
+    om = 0.5f * (du * (na.x / na.z + nb.x / nb.z) + (na.y / na.z + nb.y / nb.z));
+    w2 = 0.5f * (A * A + B * B);
+  }
+}
+
+__global__ void k_edge_setup_diag(const float4* __restrict__ nrm, const uint8_t* __restrict__ mask,
+                                  const int* __restrict__ labels, int H, int W, int persp, float fx, float fy,
+                                  float cx, float cy, float2* __restrict__ omega_d, float* __restrict__ wdr,
+                                  float* __restrict__ wdl) {
+  const int N = H * W;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
+    float2 om = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
+    const int u = a % W, v = a / W;
+    if (mask[a] && v + 1 < H) {
+      const float4 na = ldg4(&nrm[a]);
+      const float tax = persp ? (u - cx) / fx : 0.f, tay = persp ? (v - cy) / fy : 0.f;
+      const float A = persp ? (na.x * tax + na.y * tay + na.z) : na.z;
+      const float tby = persp ? (v + 1 - cy) / fy : 0.f;
+      const int la = labels[a];
+      if (u + 1 < W && mask[a + W + 1]) {
+        const float4 nb = ldg4(&nrm[a + W + 1]);
+        const float B = persp ? (nb.x * ((u + 1 - cx) / fx) + nb.y * tby + nb.z) : nb.z;
+        float w2;
+        diag_edge(na, nb, A, B, 1, persp, fx, fy, om.x, w2);
+        if (labels[a + W + 1] == la) w.x = w2;
+      }
+      if (u >= 1 && mask[a + W - 1]) {
+        const float4 nb = ldg4(&nrm[a + W - 1]);
+        const float B = persp ? (nb.x * ((u - 1 - cx) / fx) + nb.y * tby + nb.z) : nb.z;
+        float w2;
+        diag_edge(na, nb, A, B, -1, persp, fx, fy, om.y, w2);
+        if (labels[a + W - 1] == la) w.y = w2;
+      }
+    }
+    omega_d[a] = om;
+    wdr[a] = w.x;
+    wdl[a] = w.y;
+  }
+}
+
+// k_diag_rhs over the 8 neighbours: the upper-left neighbour's lower-right
+// edge is wdr[a - W - 1], the upper-right neighbour's lower-left edge
+// wdl[a - W + 1] (0 where the edge does not exist, so raster-linear indexing
+// needs no column tests).
+__global__ void k_diag_rhs8(const float* __restrict__ wr, const float* __restrict__ wd,
+                            const float2* __restrict__ omega, const float* __restrict__ wdr,
+                            const float* __restrict__ wdl, const float2* __restrict__ omega_d, int H, int W,
+                            float* __restrict__ invd, float* __restrict__ rhs) {
+  const int N = H * W;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
+    const int v = a / W;
+    const float2 om = omega[a], od = omega_d[a];
+    const float wra = wr[a], wda = wd[a], wdra = wdr[a], wdla = wdl[a];
+    float wl = 0.f, wu = 0.f, ol = 0.f, ou = 0.f, wul = 0.f, wur = 0.f, oul = 0.f, our = 0.f;
+    if (a > 0) { wl = wr[a - 1]; ol = omega[a - 1].x; }
+    if (v > 0) { wu = wd[a - W]; ou = omega[a - W].y; }
+    if (a - W - 1 >= 0) { wul = wdr[a - W - 1]; oul = omega_d[a - W - 1].x; }
+    if (v > 0) { wur = wdl[a - W + 1]; our = omega_d[a - W + 1].y; }
+    const float d = wra + wda + wl + wu + wdra + wdla + wul + wur;
+    invd[a] = d > 0.f ? 1.0f / d : 0.f;
+    rhs[a] = wra * om.x + wda * om.y - wl * ol - wu * ou + wdra * od.x + wdla * od.y - wul * oul - wur * our;
+  }
+}
+
+// BiNI reweighting of the diagonal edges (n_fill_irls > 1); the opposite
+// neighbour of a is a - (b - a), restricted to the component.
+__global__ void k_fill_reweight_diag(const float* __restrict__ ntau, const int* __restrict__ labels,
+                                     const float* __restrict__ x, int H, int W, int persp, float fx, float fy,
+                                     float k, float* __restrict__ wdr, float* __restrict__ wdl) {
+  const int N = H * W;
+  const float f = persp ? sqrtf(fx * fy) : 1.f;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
+    const int la = labels[a];
+    const int u = a % W, v = a / W;
+    if (la >= 0 && wdr[a] > 0.f) {
+      const int b = a + W + 1;
+      const float gba = f * ntau[a], gab = f * ntau[b];
+      const bool ho_a = (u > 0) && (v > 0) && labels[a - W - 1] == la;
+      const bool ho_b = (u + 2 < W) && (v + 2 < H) && labels[b + W + 1] == la;
+      wdr[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W - 1] : 0.f, ho_a, k) +
+               bini_w(gab, x[b], x[a], ho_b ? x[b + W + 1] : 0.f, ho_b, k);
+    }
+    if (la >= 0 && wdl[a] > 0.f) {
+      const int b = a + W - 1;
+      const float gba = f * ntau[a], gab = f * ntau[b];
+      const bool ho_a = (u + 1 < W) && (v > 0) && labels[a - W + 1] == la;
+      const bool ho_b = (u >= 2) && (v + 2 < H) && labels[b + W - 1] == la;
+      wdl[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W + 1] : 0.f, ho_a, k) +
+               bini_w(gab, x[b], x[a], ho_b ? x[b + W - 1] : 0.f, ho_b, k);
+    }
+  }
+}
+
 // Per-component sums (slot0 += val, slot1 += 1) over valid pixels.
 __global__ void k_comp_sum(const int* __restrict__ labels, const float* __restrict__ val, int N,
                            double* __restrict__ acc) {
@@ -237,23 +343,42 @@ __device__ __forceinline__ float apply_stencil(const Stencil& s, const float* __
   return acc;
 }
 
+// The diagonal part of (A p)_a with 8-connectivity: the lower-right and
+// lower-left edges of a and the same edges of its upper-left and upper-right
+// neighbours (weights 0 where an edge does not exist).
+__device__ __forceinline__ float apply_diag(const float* __restrict__ wdr, const float* __restrict__ wdl,
+                                            const float* __restrict__ p, int a, int W, float pa) {
+  float acc = 0.f;
+  const float w0 = wdr[a], w1 = wdl[a];
+  const float w2 = (a - W - 1 >= 0) ? wdr[a - W - 1] : 0.f;
+  const float w3 = (a - W + 1 >= 0) ? wdl[a - W + 1] : 0.f;
+  if (w0 != 0.f) acc += w0 * (pa - p[a + W + 1]);
+  if (w1 != 0.f) acc += w1 * (pa - p[a + W - 1]);
+  if (w2 != 0.f) acc += w2 * (pa - p[a - W - 1]);
+  if (w3 != 0.f) acc += w3 * (pa - p[a - W + 1]);
+  return acc;
+}
+
 template <typename Acc>
 __device__ __forceinline__ void block_atomic_add(double* dst, Acc v, double* sh) {
   double t = block_sum_d((double)v, sh);
   if (threadIdx.x == 0 && t != 0.0) atomicAdd(dst, t);
 }
 
-template <typename Acc>
+template <typename Acc, int CONN = 4>
 __global__ void k_cg_init(const float* __restrict__ wr, const float* __restrict__ wd,
                           const float* __restrict__ invd, const float* __restrict__ rhs,
                           const float* __restrict__ x, float* __restrict__ r, float* __restrict__ p, int H,
-                          int W, DevState* st) {
+                          int W, DevState* st, const float* __restrict__ wdr = nullptr,
+                          const float* __restrict__ wdl = nullptr) {
   __shared__ double sh[33];
   const int N = H * W;
   Acc rz = 0, rr = 0, bb = 0;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     Stencil s = load_stencil(wr, wd, a, W);
-    float ra = rhs[a] - apply_stencil(s, x, a, W, x[a]);
+    float ax = apply_stencil(s, x, a, W, x[a]);
+    if constexpr (CONN == 8) ax += apply_diag(wdr, wdl, x, a, W, x[a]);
+    float ra = rhs[a] - ax;
     if (invd[a] == 0.f) ra = 0.f;
     float z = ra * invd[a];
     r[a] = ra;
@@ -275,9 +400,10 @@ __global__ void k_cg_init_done(DevState* st, double tol2) {
   st->cg[CG_RZNEW] = 0.0;
 }
 
-template <typename Acc>
+template <typename Acc, int CONN = 4>
 __global__ void k_cg_spmv(const float* __restrict__ wr, const float* __restrict__ wd,
-                          const float* __restrict__ p, float* __restrict__ q, int H, int W, DevState* st) {
+                          const float* __restrict__ p, float* __restrict__ q, int H, int W, DevState* st,
+                          const float* __restrict__ wdr = nullptr, const float* __restrict__ wdl = nullptr) {
   __shared__ double sh[33];
   if (*(volatile int*)&st->cg_done) return;
   const int N = H * W;
@@ -285,10 +411,17 @@ __global__ void k_cg_spmv(const float* __restrict__ wr, const float* __restrict_
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     Stencil s = load_stencil(wr, wd, a, W);
     const float pa = p[a];
-    q[a] = apply_stencil(s, p, a, W, pa);
+    float qa = apply_stencil(s, p, a, W, pa);
+    if constexpr (CONN == 8) qa += apply_diag(wdr, wdl, p, a, W, pa);
+    q[a] = qa;
     // p^T A p as the sum over edges of w (p_a - p_b)^2 (no cancellation)
     if (s.wr != 0.f) { float d = pa - p[a + 1]; pap += (Acc)(s.wr * d * d); }
     if (s.wd != 0.f) { float d = pa - p[a + W]; pap += (Acc)(s.wd * d * d); }
+    if constexpr (CONN == 8) {
+      const float w0 = wdr[a], w1 = wdl[a];
+      if (w0 != 0.f) { float d = pa - p[a + W + 1]; pap += (Acc)(w0 * d * d); }
+      if (w1 != 0.f) { float d = pa - p[a + W - 1]; pap += (Acc)(w1 * d * d); }
+    }
   }
   block_atomic_add(&st->cg[CG_PAP], pap, sh);
 }
@@ -767,7 +900,14 @@ ni_status fill_setup_launch(ni_handle* h, cudaStream_t s) {
   const int N = h->N;
   k_edge_setup<<<grid_px(h, N), 256, 0, s>>>(h->normals, h->mask, h->labels, h->H, h->W, h->persp, h->fx, h->fy,
                                                h->cx, h->cy, h->omega, h->ntau, h->wr, h->wd); NI_COUNT(h);
-  k_diag_rhs<<<grid_px(h, N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+  if (h->cfg.connectivity == 8) {
+    k_edge_setup_diag<<<grid_px(h, N), 256, 0, s>>>(h->normals, h->mask, h->labels, h->H, h->W, h->persp, h->fx,
+                                                      h->fy, h->cx, h->cy, h->omega_d, h->wdr, h->wdl); NI_COUNT(h);
+    k_diag_rhs8<<<grid_px(h, N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->wdr, h->wdl, h->omega_d, h->H, h->W,
+                                                h->invd, h->b); NI_COUNT(h);
+  } else {
+    k_diag_rhs<<<grid_px(h, N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+  }
   k_tile_labels<<<grid_px(h, (long long)h->ntiles * 256), 256, 0, s>>>(h->labels, h->ntiles, h->ntx, h->H, h->W,
                                                                         h->tile_lab); NI_COUNT(h);
   return ni_cuda_check(h, cudaGetLastError(), "fill setup");
@@ -789,8 +929,15 @@ static ni_status plain_solve(ni_handle* h, cudaStream_t s) {
   cudaMemsetAsync(&h->st->cg[0], 0, sizeof(double) * 8, s);
   cudaMemsetAsync(&h->st->bar2, 0, sizeof(GridBar), s);
   const bool f64 = h->cfg.precision == 0;
-  if (f64) k_cg_init<double><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
-  else k_cg_init<float><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
+  const bool c8 = h->cfg.connectivity == 8;
+  const float *wdr = h->wdr, *wdl = h->wdl;
+  if (c8) {
+    if (f64) k_cg_init<double, 8><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st, wdr, wdl);
+    else k_cg_init<float, 8><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st, wdr, wdl);
+  } else {
+    if (f64) k_cg_init<double><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
+    else k_cg_init<float><<<g, 256, 0, s>>>(h->wr, h->wd, h->invd, h->b, h->x, h->r, h->p, H, W, h->st);
+  }
   NI_COUNT(h);
   k_cg_init_done<<<1, 1, 0, s>>>(h->st, tol2); NI_COUNT(h);
   ni_status rc = ni_cuda_check(h, cudaGetLastError(), "plain PCG init");
@@ -804,8 +951,13 @@ static ni_status plain_solve(ni_handle* h, cudaStream_t s) {
   cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   const long long launches_before = h->launches;
   for (int i = 0; i < CHUNK; ++i) {
-    if (f64) k_cg_spmv<double><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
-    else k_cg_spmv<float><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
+    if (c8) {
+      if (f64) k_cg_spmv<double, 8><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st, wdr, wdl);
+      else k_cg_spmv<float, 8><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st, wdr, wdl);
+    } else {
+      if (f64) k_cg_spmv<double><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
+      else k_cg_spmv<float><<<g, 256, 0, cs>>>(h->wr, h->wd, h->p, h->q, H, W, h->st);
+    }
     NI_COUNT(h);
     if (f64) k_cg_update<double><<<g, 256, 0, cs>>>(h->invd, h->p, h->q, h->x, h->r, N, h->st);
     else k_cg_update<float><<<g, 256, 0, cs>>>(h->invd, h->p, h->q, h->x, h->r, N, h->st);
@@ -889,7 +1041,15 @@ ni_status fill_solve_launch(ni_handle* h, cudaStream_t s) {
     if (sweep > 0) {
       k_fill_reweight<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp, h->fx,
                                                         h->fy, (float)h->cfg.k, h->wr, h->wd); NI_COUNT(h);
-      k_diag_rhs<<<grid_px(h, h->N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+      if (h->cfg.connectivity == 8) {
+        k_fill_reweight_diag<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp,
+                                                                h->fx, h->fy, (float)h->cfg.k, h->wdr, h->wdl);
+        NI_COUNT(h);
+        k_diag_rhs8<<<grid_px(h, h->N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->wdr, h->wdl, h->omega_d, h->H,
+                                                       h->W, h->invd, h->b); NI_COUNT(h);
+      } else {
+        k_diag_rhs<<<grid_px(h, h->N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->H, h->W, h->invd, h->b); NI_COUNT(h);
+      }
       rc = project_rhs(h, h->b, s);
       if (rc != NI_OK) return rc;
     }

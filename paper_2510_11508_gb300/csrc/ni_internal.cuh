@@ -95,6 +95,11 @@ struct ni_handle {
   float* ntau = nullptr;       // n_a . tau_a (n_az for orthographic)
   float* wr = nullptr;         // combined fill weight of the edge to the right
   float* wd = nullptr;         // combined fill weight of the edge below
+  // 8-connectivity only (NULL otherwise): the diagonal edges of pixel a, to the
+  // lower-right (a + W + 1) and lower-left (a + W - 1) neighbour
+  float2* omega_d = nullptr;   // omega~_{b->a} of the lower-right (x) and lower-left (y) edge
+  float* wdr = nullptr;        // combined fill weight of the lower-right edge
+  float* wdl = nullptr;        // combined fill weight of the lower-left edge
   float* invd = nullptr;       // 1 / Jacobi diagonal (0 where the diagonal is 0)
   float* x = nullptr;          // log-depth relative to the component offset
   float* r = nullptr;

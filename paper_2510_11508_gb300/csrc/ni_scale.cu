@@ -2,7 +2,8 @@
 //
 // Partition structures (rebuilt after seeding and after every merge):
 //   E_inter   inter-component edges as edge ids 2 a + dir (dir 0 right, 1 down),
-//             in increasing id order (stream compaction);
+//             in increasing id order (stream compaction); with 8-connectivity
+//             4 a + dir (2 lower-right, 3 lower-left);
 //   pairs     the distinct component pairs (lo < hi) that inter edges join:
 //             edges are sorted by the key lo * K + hi with a stable LSD radix
 //             sort, so each pair's edges are one contiguous run;
@@ -93,7 +94,20 @@ static void compact(ni_handle* h, F f, const int* n_ptr, int* total_out, const i
   k_chunk_emit<F><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, n_ptr, h->blk, gate); NI_COUNT(h);
 }
 
+// Edge ids: CONN 4: e = 2 a + dir (0 right, 1 down); CONN 8: e = 4 a + dir
+// (2 lower-right, 3 lower-left).  b = a + step(dir).
+template <int CONN>
+__device__ __forceinline__ int edge_a(int e) { return CONN == 8 ? (e >> 2) : (e >> 1); }
+template <int CONN>
+__device__ __forceinline__ int edge_dir(int e) { return CONN == 8 ? (e & 3) : (e & 1); }
+template <int CONN>
+__device__ __forceinline__ int edge_step(int dir, int W) {
+  if constexpr (CONN == 8) return dir == 0 ? 1 : (dir == 1 ? W : (dir == 2 ? W + 1 : W - 1));
+  return dir ? W : 1;
+}
+
 // inter edges from the pixel grid (first partition)
+template <int CONN>
 struct InterFromPixels {
   const int* labels;
   int H, W;
@@ -104,24 +118,36 @@ struct InterFromPixels {
     int u = a % W, v = a / W, c = 0;
     if (u + 1 < W) { int lb = labels[a + 1]; c += (lb >= 0 && lb != la); }
     if (v + 1 < H) { int lb = labels[a + W]; c += (lb >= 0 && lb != la); }
+    if constexpr (CONN == 8) {
+      if (u + 1 < W && v + 1 < H) { int lb = labels[a + W + 1]; c += (lb >= 0 && lb != la); }
+      if (u >= 1 && v + 1 < H) { int lb = labels[a + W - 1]; c += (lb >= 0 && lb != la); }
+    }
     return c;
   }
   __device__ void emit(int a, int pos, int cnt) const {
     if (!cnt) return;
     int la = labels[a], u = a % W, v = a / W;
-    if (u + 1 < W) { int lb = labels[a + 1]; if (lb >= 0 && lb != la) out[pos++] = 2 * a; }
-    if (v + 1 < H) { int lb = labels[a + W]; if (lb >= 0 && lb != la) out[pos++] = 2 * a + 1; }
+    if constexpr (CONN == 8) {
+      if (u + 1 < W) { int lb = labels[a + 1]; if (lb >= 0 && lb != la) out[pos++] = 4 * a; }
+      if (v + 1 < H) { int lb = labels[a + W]; if (lb >= 0 && lb != la) out[pos++] = 4 * a + 1; }
+      if (u + 1 < W && v + 1 < H) { int lb = labels[a + W + 1]; if (lb >= 0 && lb != la) out[pos++] = 4 * a + 2; }
+      if (u >= 1 && v + 1 < H) { int lb = labels[a + W - 1]; if (lb >= 0 && lb != la) out[pos++] = 4 * a + 3; }
+    } else {
+      if (u + 1 < W) { int lb = labels[a + 1]; if (lb >= 0 && lb != la) out[pos++] = 2 * a; }
+      if (v + 1 < H) { int lb = labels[a + W]; if (lb >= 0 && lb != la) out[pos++] = 2 * a + 1; }
+    }
   }
 };
 
 // inter edges that survive a merge (labels already rewritten)
+template <int CONN>
 struct InterFilter {
   const int* labels;
   const int* in;
   int* out;
   int W;
   __device__ int count(int j) const {
-    int e = in[j], a = e >> 1, b = a + ((e & 1) ? W : 1);
+    int e = in[j], a = edge_a<CONN>(e), b = a + edge_step<CONN>(edge_dir<CONN>(e), W);
     return labels[a] != labels[b];
   }
   __device__ void emit(int j, int pos, int cnt) const {
@@ -285,6 +311,7 @@ static void radix_sort(ni_handle* h, unsigned long long* k0, int* v0, unsigned l
 // ---------------------------------------------------------------------------
 // partition structures
 // ---------------------------------------------------------------------------
+template <int CONN>
 __global__ void k_edge_keys(const int* __restrict__ e_id, const int* __restrict__ labels, int W,
                             DevState* st, unsigned long long* __restrict__ key, int* __restrict__ val,
                             const int* gate) {
@@ -292,7 +319,7 @@ __global__ void k_edge_keys(const int* __restrict__ e_id, const int* __restrict_
   const int n = st->nE;
   const unsigned long long K = (unsigned long long)st->K;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    int e = e_id[j], a = e >> 1, b = a + ((e & 1) ? W : 1);
+    int e = e_id[j], a = edge_a<CONN>(e), b = a + edge_step<CONN>(edge_dir<CONN>(e), W);
     unsigned long long la = (unsigned long long)labels[a], lb = (unsigned long long)labels[b];
     unsigned long long lo = la < lb ? la : lb, hi = la < lb ? lb : la;
     key[j] = lo * K + hi;
@@ -352,7 +379,11 @@ __global__ void k_copy1(const int* in, int* out, const int* gate) {
 static void build_pairs(ni_handle* h, const int* gate, cudaStream_t s) {
   DevState* st = h->st;
   const int g = grid_lin(h, h->Ecap);
-  k_edge_keys<<<g, 256, 0, s>>>(h->e_id, h->labels, h->W, st, h->e_key, h->e_val, gate); NI_COUNT(h);
+  if (h->cfg.connectivity == 8)
+    k_edge_keys<8><<<g, 256, 0, s>>>(h->e_id, h->labels, h->W, st, h->e_key, h->e_val, gate);
+  else
+    k_edge_keys<4><<<g, 256, 0, s>>>(h->e_id, h->labels, h->W, st, h->e_key, h->e_val, gate);
+  NI_COUNT(h);
   radix_sort(h, h->e_key, h->e_val, h->e_key2, h->e_val2, &st->nE, h->sort_passes, gate, s);
   PairHeads ph{h->e_key, st, h->e_pair, h->p_lo, h->p_hi};
   compact(h, ph, &st->nE, &st->nP, gate, s);
@@ -363,14 +394,16 @@ static void build_pairs(ni_handle* h, const int* gate, cudaStream_t s) {
   k_csr_finish<<<g, 256, 0, s>>>(h->e_key2, h->e_val2, st, h->csr_col, h->csr_pair, h->row_ptr, gate); NI_COUNT(h);
 }
 
-ni_status partition_build_launch(ni_handle* h, int first, cudaStream_t s) {
+template <int CONN>
+static ni_status partition_build(ni_handle* h, int first, cudaStream_t s) {
   DevState* st = h->st;
   if (first) {
     // count, size the edge buffers, then emit
-    InterFromPixels f{h->labels, h->H, h->W, nullptr};
+    InterFromPixels<CONN> f{h->labels, h->H, h->W, nullptr};
     int* nptr = h->d_count + 1;
     cudaMemcpyAsync(nptr, &h->N, sizeof(int), cudaMemcpyHostToDevice, s);
-    k_chunk_count<InterFromPixels><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, nptr, h->blk, nullptr); NI_COUNT(h);
+    k_chunk_count<InterFromPixels<CONN>><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, nptr, h->blk, nullptr);
+    NI_COUNT(h);
     k_scan_blocks_gated<<<1, 1024, 0, s>>>(h->blk, NI_SCAN_BLOCKS, &st->nE, nullptr); NI_COUNT(h);
     cudaMemcpyAsync(&h->st_host->nE, &st->nE, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -378,10 +411,11 @@ ni_status partition_build_launch(ni_handle* h, int first, cudaStream_t s) {
     ni_status rc = ensure_edge_capacity(h, h->st_host->nE);
     if (rc != NI_OK) return rc;
     f.out = h->e_id;
-    k_chunk_emit<InterFromPixels><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, nptr, h->blk, nullptr); NI_COUNT(h);
+    k_chunk_emit<InterFromPixels<CONN>><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, nptr, h->blk, nullptr);
+    NI_COUNT(h);
     build_pairs(h, nullptr, s);
   } else {
-    InterFilter f{h->labels, h->e_id, h->e_id2, h->W};
+    InterFilter<CONN> f{h->labels, h->e_id, h->e_id2, h->W};
     int* nold = h->d_count + 2;
     k_copy1<<<1, 1, 0, s>>>(&st->nE, nold, &st->gate); NI_COUNT(h);
     compact(h, f, nold, &st->nE, &st->gate, s);
@@ -389,6 +423,10 @@ ni_status partition_build_launch(ni_handle* h, int first, cudaStream_t s) {
     build_pairs(h, &st->gate, s);
   }
   return ni_cuda_check(h, cudaGetLastError(), "partition build");
+}
+
+ni_status partition_build_launch(ni_handle* h, int first, cudaStream_t s) {
+  return h->cfg.connectivity == 8 ? partition_build<8>(h, first, s) : partition_build<4>(h, first, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -403,6 +441,7 @@ struct EdgeArgs {
   const float* x;
   const double* soff;
   const float2* omega;
+  const float2* omega_d;   // diagonal edges (8-connectivity), else NULL
   const float* ntau;
   double* p_acc;
   DevState* st;
@@ -419,6 +458,7 @@ __global__ void k_pair_zero(double* __restrict__ acc, DevState* st) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc[i] = 0.0;
 }
 
+template <int CONN>
 __global__ void k_edge_accum(EdgeArgs A) {
   DevState* st = A.st;
   if (st->converged) return;
@@ -432,22 +472,39 @@ __global__ void k_edge_accum(EdgeArgs A) {
     if (j < n) {
       pair = A.e_pair[j];
       const int e = A.e_id[A.e_val[j]];
-      const int a = e >> 1, dir = e & 1, step = dir ? W : 1, b = a + step;
+      const int a = edge_a<CONN>(e), dir = edge_dir<CONN>(e), step = edge_step<CONN>(dir, W), b = a + step;
       const int ca = A.labels[a], cb = A.labels[b];
       const double za = (double)A.x[a] + A.soff[ca];
       const double zb = (double)A.x[b] + A.soff[cb];
-      const float2 om2 = A.omega[a];
-      const double rho = za - zb - (double)(dir ? om2.y : om2.x);
+      double omv;
+      if constexpr (CONN == 8) {
+        const float2 om2 = dir >= 2 ? A.omega_d[a] : A.omega[a];
+        omv = (double)((dir & 1) ? om2.y : om2.x);
+      } else {
+        const float2 om2 = A.omega[a];
+        omv = (double)(dir ? om2.y : om2.x);
+      }
+      const double rho = za - zb - omv;
       double w;
       if (t <= 1) {
         w = 2.0;   // two rows of unit weight (alignment iterations)
       } else {
         const int u = a % W, vv = a / W;
-        const double f = A.persp ? (dir ? A.fy : A.fx) : 1.0;
+        double f;
+        bool has_oa, has_ob;
+        if constexpr (CONN == 8) {
+          // f = sqrt(f_x f_y) on diagonals; -b of a diagonal edge is a - (b - a)
+          f = A.persp ? (dir == 0 ? A.fx : (dir == 1 ? A.fy : sqrt(A.fx * A.fy))) : 1.0;
+          has_oa = dir == 0 ? (u > 0) : dir == 1 ? (vv > 0) : dir == 2 ? (u > 0 && vv > 0) : (u + 1 < W && vv > 0);
+          has_ob = dir == 0 ? (u + 2 < W) : dir == 1 ? (vv + 2 < H)
+                   : dir == 2 ? (u + 2 < W && vv + 2 < H) : (u >= 2 && vv + 2 < H);
+        } else {
+          f = A.persp ? (dir ? A.fy : A.fx) : 1.0;
+          // opposite neighbour of a (away from b) and of b (away from a)
+          has_oa = dir ? (vv > 0) : (u > 0);
+          has_ob = dir ? (vv + 2 < H) : (u + 2 < W);
+        }
         const double gba = f * (double)A.ntau[a], gab = f * (double)A.ntau[b];
-        // opposite neighbour of a (away from b) and of b (away from a)
-        const bool has_oa = dir ? (vv > 0) : (u > 0);
-        const bool has_ob = dir ? (vv + 2 < H) : (u + 2 < W);
         double doa = 0.0, dob = 0.0;
         if (has_oa) {
           int o = a - step, co = A.labels[o];
@@ -724,11 +781,14 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   k_pair_zero<<<ge, 256, 0, s>>>(h->p_acc, st); NI_COUNT(h);
   EdgeArgs ea;
   ea.e_id = h->e_id; ea.e_val = h->e_val; ea.e_pair = h->e_pair; ea.p_lo = h->p_lo;
-  ea.labels = h->labels; ea.x = h->x; ea.soff = h->soff; ea.omega = h->omega; ea.ntau = h->ntau;
+  ea.labels = h->labels; ea.x = h->x; ea.soff = h->soff; ea.omega = h->omega; ea.omega_d = h->omega_d;
+  ea.ntau = h->ntau;
   ea.p_acc = h->p_acc; ea.st = st; ea.H = h->H; ea.W = h->W; ea.persp = h->persp;
   ea.fx = h->cfg.cam.fx; ea.fy = h->cfg.cam.fy; ea.k = h->cfg.k;
   ea.Lt = log10(h->cfg.L); ea.Ut = log10(h->cfg.U); ea.U = h->cfg.U; ea.hard = h->cfg.hard_outliers;
-  k_edge_accum<<<ge, 256, 0, s>>>(ea); NI_COUNT(h);
+  if (h->cfg.connectivity == 8) k_edge_accum<8><<<ge, 256, 0, s>>>(ea);
+  else k_edge_accum<4><<<ge, 256, 0, s>>>(ea);
+  NI_COUNT(h);
   k_node_assemble<<<grid_lin(h, 32LL * h->Kcap), 256, 0, s>>>(h->row_ptr, h->csr_pair, h->p_lo, h->p_acc, st,
                                                         h->sd, h->sv + 5 * (size_t)h->Kcap,
                                                         h->sv + 6 * (size_t)h->Kcap, h->csr_w); NI_COUNT(h);
@@ -775,21 +835,27 @@ __global__ void k_merge_init(DevState* st, unsigned long long* __restrict__ key,
   }
 }
 
+// chi_abs (caller-given |chi|): [H][W][2] (right, down) with 4-connectivity,
+// [H][W][4] (right, down, lower-right, lower-left) with 8.
+template <int CONN>
 __global__ void k_merge_keys(const int* __restrict__ e_id, const int* __restrict__ labels,
                              const float* __restrict__ x, const double* __restrict__ soff,
-                             const float2* __restrict__ omega, const float* __restrict__ chi_abs, int W,
-                             DevState* st, unsigned long long* __restrict__ key) {
+                             const float2* __restrict__ omega, const float2* __restrict__ omega_d,
+                             const float* __restrict__ chi_abs, int W, DevState* st,
+                             unsigned long long* __restrict__ key) {
   if (!st->gate) return;
   const int n = st->nE;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const int e = e_id[j], a = e >> 1, dir = e & 1, b = a + (dir ? W : 1);
+    const int e = e_id[j], a = edge_a<CONN>(e), dir = edge_dir<CONN>(e), b = a + edge_step<CONN>(dir, W);
     const int ca = labels[a], cb = labels[b];
     float chi;
     if (chi_abs) {
-      chi = fabsf(chi_abs[2 * (size_t)a + dir]);
+      chi = fabsf(chi_abs[(CONN == 8 ? 4 : 2) * (size_t)a + dir]);
     } else {
-      const float2 om = omega[a];
-      const double rho = ((double)x[a] + soff[ca]) - ((double)x[b] + soff[cb]) - (double)(dir ? om.y : om.x);
+      float2 om;
+      if constexpr (CONN == 8) om = dir >= 2 ? omega_d[a] : omega[a];
+      else om = omega[a];
+      const double rho = ((double)x[a] + soff[ca]) - ((double)x[b] + soff[cb]) - (double)((dir & 1) ? om.y : om.x);
       chi = (float)fabs(rho);
     }
     const unsigned long long k = ((unsigned long long)__float_as_uint(chi) << 32) | (unsigned int)e;
@@ -798,6 +864,7 @@ __global__ void k_merge_keys(const int* __restrict__ e_id, const int* __restrict
   }
 }
 
+template <int CONN>
 __global__ void k_merge_link(const unsigned long long* __restrict__ key, const int* __restrict__ labels,
                              int W, DevState* st, int* __restrict__ kparent) {
   if (!st->gate) return;
@@ -805,7 +872,7 @@ __global__ void k_merge_link(const unsigned long long* __restrict__ key, const i
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < K; c += gridDim.x * blockDim.x) {
     const unsigned long long k = key[c];
     if (k == ~0ull) continue;
-    const int e = (int)(k & 0xffffffffull), a = e >> 1, b = a + ((e & 1) ? W : 1);
+    const int e = (int)(k & 0xffffffffull), a = edge_a<CONN>(e), b = a + edge_step<CONN>(edge_dir<CONN>(e), W);
     const int ca = labels[a], cb = labels[b];
     uf_unite(kparent, c, ca == c ? cb : ca);
   }
@@ -871,8 +938,15 @@ ni_status merge_launch(ni_handle* h, const float* chi_abs, cudaStream_t s) {
   const int gk = grid_lin(h, h->Kcap), ge = grid_lin(h, h->Ecap), gp = grid_lin(h, h->N);
   int* knew = h->d_count + 3;
   k_merge_init<<<gk, 256, 0, s>>>(st, h->kkey, h->kparent); NI_COUNT(h);
-  k_merge_keys<<<ge, 256, 0, s>>>(h->e_id, h->labels, h->x, h->soff, h->omega, chi_abs, h->W, st, h->kkey); NI_COUNT(h);
-  k_merge_link<<<gk, 256, 0, s>>>(h->kkey, h->labels, h->W, st, h->kparent); NI_COUNT(h);
+  if (h->cfg.connectivity == 8) {
+    k_merge_keys<8><<<ge, 256, 0, s>>>(h->e_id, h->labels, h->x, h->soff, h->omega, h->omega_d, chi_abs, h->W, st,
+                                       h->kkey); NI_COUNT(h);
+    k_merge_link<8><<<gk, 256, 0, s>>>(h->kkey, h->labels, h->W, st, h->kparent); NI_COUNT(h);
+  } else {
+    k_merge_keys<4><<<ge, 256, 0, s>>>(h->e_id, h->labels, h->x, h->soff, h->omega, nullptr, chi_abs, h->W, st,
+                                       h->kkey); NI_COUNT(h);
+    k_merge_link<4><<<gk, 256, 0, s>>>(h->kkey, h->labels, h->W, st, h->kparent); NI_COUNT(h);
+  }
   k_merge_compress<<<gk, 256, 0, s>>>(st, h->kparent); NI_COUNT(h);
   KRoots kr{h->kparent, h->kmap};
   compact(h, kr, &st->K, knew, &st->gate, s);

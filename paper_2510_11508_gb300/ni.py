@@ -226,7 +226,7 @@ class Integrator:
         return labels, K.value
 
     def merge_residuals(self, chi_abs: torch.Tensor) -> Tuple[torch.Tensor, int]:
-        _check_dev(chi_abs, torch.float32, (self.H, self.W, 2), "chi_abs")
+        _check_dev(chi_abs, torch.float32, (self.H, self.W, 4 if self.cfg.connectivity == 8 else 2), "chi_abs")
         labels = torch.empty((self.H, self.W), dtype=torch.int32, device=self.device)
         K = C.c_int32()
         self._raise(self.L.ni_merge_residuals(self.h, chi_abs.data_ptr(), labels.data_ptr(), C.byref(K),

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def _check(normals, mask, camera, theta):
     H, W = mask.shape
     n, m = dev(normals, mask)
-    it = integrator(H, W, camera, {"theta_c_deg": theta}, validate=0, connectivity=8)
+    it = integrator(H, W, camera, {"theta_c_deg": theta}, validate=0, connectivity=8, batched=0)
     lab, K = it.seed_components(n, m)
     ref, Kr = O.seed_components(normals, mask, theta, 8)
     assert K == Kr
@@ -86,7 +86,7 @@ def test_later_stages_refuse_connectivity_8():
     w = make_workload("c1")
     H, W = w.mask.shape
     n, m = dev(w.normals, w.mask)
-    it = integrator(H, W, w.camera, w.params, connectivity=8)
+    it = integrator(H, W, w.camera, w.params, connectivity=8, batched=0)
     it.seed_components(n, m)
     with pytest.raises(ni.NIError) as ei:
         it.solve_components()
