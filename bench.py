@@ -52,8 +52,6 @@ def parse():
     ap.add_argument("--variant", default="batched", choices=["batched", "plain"])
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--precond", type=int, default=1, help="batched fill: 0 Jacobi, 1 multigrid")
-    ap.add_argument("--scale-precond", type=int, default=0,
-                    help="relative-scale PCG: 0 Jacobi, 1 quotient-graph multigrid")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle accuracy check")
     ap.add_argument("--pixel-level", action="store_true",
                     help="theta_c = None: every pixel its own component (the paper's pixel-level setting)")
@@ -209,7 +207,7 @@ def run_ours(args):
     if args.pixel_level:
         params["theta_c_deg"] = None
     cfg = ni.config_for(H, W, w.camera, params, batched=1 if args.variant == "batched" else 0,
-                        precision=args.precision, precond=args.precond, scale_precond=args.scale_precond)
+                        precision=args.precision, precond=args.precond)
     it = ni.Integrator(cfg)
     n = torch.from_numpy(w.normals).cuda()
     m = torch.from_numpy(w.mask).cuda()
@@ -320,7 +318,6 @@ def run_ours(args):
                        "n_valid": n_valid, "variant": args.variant,
                        "fill_preconditioner": ("multigrid V-cycle" if args.precond == 1 else "Jacobi")
                        if args.variant == "batched" else "Jacobi",
-                       "scale_preconditioner": "quotient-graph multigrid" if args.scale_precond == 1 else "Jacobi",
                        "reductions": "fp64" if args.precision == 0 else "fp32 tree + fp64 across CTAs",
                        "theta_c_deg": params["theta_c_deg"], "T": params["T"],
                        "can_merge": params["can_merge"], "freq_merging": params["freq_merging"],

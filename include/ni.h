@@ -108,11 +108,6 @@ typedef struct {
   int fill_kernels;         /* multigrid fill: 0 one kernel per pass, chunks of iterations
                                replayed from a CUDA graph; 1 (default) one persistent
                                cooperative kernel with software grid barriers */
-  int scale_precond;        /* preconditioner of the relative-scale PCG (Eq. 14): 0 (default)
-                               Jacobi; 1 aggregation multigrid on the quotient graph, rebuilt
-                               every iteration (up to 8192 components; Jacobi beyond).
-                               1 is experimental: not yet validated, and known to break down
-                               when the outlier weights span hundreds of decades */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

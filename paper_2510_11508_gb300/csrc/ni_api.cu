@@ -68,7 +68,6 @@ extern "C" void ni_config_default(ni_config* c, int H, int W) {
   c->mg_cta_cells = 0;
   c->mg_flags = 0;
   c->fill_kernels = 1;
-  c->scale_precond = 0;
   c->hard_outliers = 0;
   c->validate = 1;
 }
@@ -101,7 +100,6 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 8) { why = "ctas_per_sm in [0, 8]"; return NI_ERR_INVALID_ARG; }
   if (c->mg_coarse_sweeps < 0 || c->mg_coarse_sweeps > 64) { why = "mg_coarse_sweeps in [0, 64]"; return NI_ERR_INVALID_ARG; }
   if (c->fill_kernels != 0 && c->fill_kernels != 1) { why = "fill_kernels must be 0 or 1"; return NI_ERR_INVALID_ARG; }
-  if (c->scale_precond != 0 && c->scale_precond != 1) { why = "scale_precond must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;
@@ -259,7 +257,6 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   dfree(h->tile_in); dfree(h->tile_out);
   free_mg(h);
   free_made(h);
-  free_scale_mg(h);
   if (h->net) ni_cnn_destroy(h->net);
   if (h->st_host) cudaFreeHost(h->st_host);
   for (int i = 0; i < 8; ++i)

@@ -191,8 +191,6 @@ struct ni_handle {
 
   // scratch of ni_min_made (allocated on first use)
   struct MadeScratch* made = nullptr;
-  // scratch of the quotient-graph multigrid (scale_precond = 1)
-  struct ScaleMgScratch* smg = nullptr;
 
   // device copies for ni_integrate_host
   float4* in_normals = nullptr;
@@ -244,12 +242,6 @@ ni_status ensure_component_capacity(ni_handle* h, int K);
 
 // ni_made.cu
 void free_made(ni_handle* h);
-
-// ni_scale_mg.cu
-bool scale_mg_usable(ni_handle* h);
-ni_status scale_mg_prepare(ni_handle* h);
-ni_status scale_mg_launch(ni_handle* h, double* diag, double* g, double* gabs, double* sv, cudaStream_t s);
-void free_scale_mg(ni_handle* h);
 
 // ni_cnn.cu
 ni_status warm_start_launch(ni_handle* h, cudaStream_t s);

@@ -414,8 +414,6 @@ static ni_status partition_build(ni_handle* h, int first, cudaStream_t s) {
     k_chunk_emit<InterFromPixels<CONN>><<<NI_SCAN_BLOCKS, NI_SCAN_THREADS, 0, s>>>(f, nptr, h->blk, nullptr);
     NI_COUNT(h);
     build_pairs(h, nullptr, s);
-    rc = scale_mg_prepare(h);
-    if (rc != NI_OK) return rc;
   } else {
     InterFilter<CONN> f{h->labels, h->e_id, h->e_id2, h->W};
     int* nold = h->d_count + 2;
@@ -807,11 +805,6 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   sa.maxit = h->cfg.scale_maxit > 0 ? h->cfg.scale_maxit : std::min(4 * h->Kcap + 100, 200000);
   sa.T = h->cfg.T;
   sa.dE_max = h->cfg.dE_max;
-  if (scale_mg_usable(h)) {
-    ni_status rc = scale_mg_launch(h, h->sd, h->sv + 5 * (size_t)h->Kcap, h->sv + 6 * (size_t)h->Kcap, h->sv, s);
-    if (rc != NI_OK) return rc;
-    return ni_cuda_check(h, cudaGetLastError(), "scale iteration");
-  }
   const int grid = scale_cg_grid(h);
   if (grid == 1) {
     k_scale_cg<<<1, 1024, 0, s>>>(sa); NI_COUNT(h);

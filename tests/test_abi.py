@@ -53,14 +53,13 @@ def test_struct_layout_matches_header(lib, tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "l.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ni.h"\nint main(){'
-                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ni_config), sizeof(ni_stats),'
-                   ' offsetof(ni_config, cg_rtol), offsetof(ni_stats, energy), offsetof(ni_config, fill_kernels),'
-                   ' offsetof(ni_config, scale_precond));}')
+                   'printf("%zu %zu %zu %zu %zu\\n", sizeof(ni_config), sizeof(ni_stats),'
+                   ' offsetof(ni_config, cg_rtol), offsetof(ni_stats, energy), offsetof(ni_config, fill_kernels));}')
     exe = tmp_path / "l"
     subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     out = subprocess.check_output([str(exe)]).decode().split()
     exp = [C.sizeof(ni.Config), C.sizeof(ni.Stats), ni.Config.cg_rtol.offset,
-           ni.Stats.energy.offset, ni.Config.fill_kernels.offset, ni.Config.scale_precond.offset]
+           ni.Stats.energy.offset, ni.Config.fill_kernels.offset]
     assert [int(v) for v in out] == exp
 
 
@@ -79,7 +78,7 @@ def test_no_oracle_in_product_path():
     ("connectivity", 8),   # 8-connectivity needs batched = 0 (the default is 1)
     ("T", 0), ("T", 1000), ("precision", 2), ("precond", 2),
     ("mg_omega", 1.0), ("mg_correction", 4.0), ("ctas_per_sm", 9), ("fill_kernels", 2),
-    ("mg_coarse_sweeps", 100), ("cg_maxit", 0), ("n_fill_irls", 0), ("dE_max", -1.0), ("scale_precond", 2),
+    ("mg_coarse_sweeps", 100), ("cg_maxit", 0), ("n_fill_irls", 0), ("dE_max", -1.0),
 ])
 def test_invalid_config_rejected_before_any_device_call(lib, field, value):
     """ni_create validates the whole config on the host and returns
