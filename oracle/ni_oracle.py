@@ -212,6 +212,9 @@ def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
     is taken as 0.
     a, b: endpoints with b = a + step(d) or b = a - step(d); the opposite
     neighbour is a - (b - a).
+    Pinned: limits and worked values of the sigmoid form, the opposite
+    neighbour on each side, and the same-component branch
+    (tests/test_oracle_pins.py, tests/test_oracle_scale_rows_pins.py).
     """
     step = b - a
     ob = a - step
@@ -447,7 +450,10 @@ def scale_system(geo: Geometry, labels, K, zt, t, params: Params, e=None):
         row (a->b): +1 at pi(b), -1 at pi(a), rhs w~_{a->b} - (z~_b - z~_a)
     Weights: 1 for t <= 1 (alignment, Sec. 3.4); for t > 1 the BiNI weight W
     (Eq. 5) times W^out (Eq. 11) of |chi^(t-1)|, the residual at the current z~.
-    Reading: z~ inside W is the current z~, and -b may be any valid pixel."""
+    Reading: z~ inside W is the current z~, and -b may be any valid pixel.
+    Pinned: every row of a 3-component map written out by hand at t = 2
+    (tests/test_oracle_scale_rows_pins.py) and the dense least-squares solve
+    of the same rows (tests/test_oracle_pins.py)."""
     if e is None:
         e = inter_edges(geo, labels)
     a, b = geo.a[e], geo.b[e]
