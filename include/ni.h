@@ -254,8 +254,11 @@ ni_status ni_load_net(ni_handle* h, const char* path);
  * run -- for example a real-time pipeline that reserves all memory at start-up,
  * a host framework whose allocator owns the device, or code where cudaMalloc
  * would synchronise the device or fail under a fixed memory-pool limit.  It
- * computes exactly what ni_seed_components computes (same kernels, same
- * canonical labels) without a handle: the union-find parent array, the scan
+ * always seeds with 4-connectivity (it takes no connectivity argument) and
+ * then computes exactly what ni_seed_components computes for a handle created
+ * with connectivity = 4 (same kernels, same canonical labels); a handle with
+ * connectivity = 8 also unites diagonal edges and gives other labels.  It
+ * needs no handle: the union-find parent array, the scan
  * partials and the counters live in one file-scope device array of
  * 16 MiB + 16 KiB that every GPU which loads this library keeps until the
  * process exits.
@@ -266,7 +269,10 @@ ni_status ni_load_net(ni_handle* h, const char* path);
  * Limit: H * W <= 4,194,304 (2^22) pixels; larger maps (and bad sizes or
  * pointers) return NI_ERR_INVALID_ARG without touching the GPU.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the life of the process; after a
+ * cudaDeviceReset (or any teardown of the device's primary context) that
+ * cached address is stale, so do not call this entry point again in such a
+ * process.  Make the first call before any stream capture.  All calls
  * share the one array, so calls that overlap on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  Asynchronous on
  * `stream`; calls no cudaMalloc, cudaFree or allocating library routine. */

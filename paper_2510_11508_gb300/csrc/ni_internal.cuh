@@ -206,6 +206,10 @@ struct ni_handle {
 #define NI_TILE_W 32
 #define NI_TILE_H 32
 #define NI_TILE_THREADS 256
+// Seeding tile of k_seed_local (one CTA of NI_SEED_TSW x NI_SEED_TSH threads per
+// tile); every launch of the seeding kernels takes its tile shape from here.
+#define NI_SEED_TSW 32
+#define NI_SEED_TSH 16
 #define NI_SCAN_BLOCKS 1024
 #define NI_SCAN_THREADS 512
 #define NI_SORT_BLOCKS 256

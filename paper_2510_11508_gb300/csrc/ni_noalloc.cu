@@ -33,7 +33,9 @@ __global__ void k_gather_labels(const int* parent, int n, int* labels);
 #define NI_NOALLOC_HEAD_BYTES 16384
 #define NI_NOALLOC_BYTES (NI_NOALLOC_HEAD_BYTES + 4 * (size_t)NI_NOALLOC_MAX_PIXELS)
 
-static_assert(sizeof(DevState) + 4 * (NI_SCAN_BLOCKS + 8) <= NI_NOALLOC_HEAD_BYTES, "scratch head too small");
+// DevState, rounded up to 256 bytes, then NI_SCAN_BLOCKS + 1 partial sums and the count
+static_assert(((sizeof(DevState) + 255) / 256) * 256 + 4 * (NI_SCAN_BLOCKS + 2) <= NI_NOALLOC_HEAD_BYTES,
+              "scratch head too small");
 
 static __device__ __align__(256) unsigned char g_scratch[NI_NOALLOC_BYTES];
 
@@ -91,8 +93,8 @@ extern "C" ni_status ni_seed_components_noalloc(const float* normals, const uint
   // the counters a previous call left behind must start at zero
   e = cudaMemsetAsync(st, 0, sizeof(DevState), s);
   if (e != cudaSuccess) return NI_ERR_CUDA;
-  const int nbx = (W + 31) / 32, nby = (H + 15) / 16;
-  k_seed_local<<<dim3(nbx, nby), 512, 0, s>>>(reinterpret_cast<const float4*>(normals), mask, H, W, cth, fx, fy,
+  const int nbx = (W + NI_SEED_TSW - 1) / NI_SEED_TSW, nby = (H + NI_SEED_TSH - 1) / NI_SEED_TSH;
+  k_seed_local<<<dim3(nbx, nby), NI_SEED_TSW * NI_SEED_TSH, 0, s>>>(reinterpret_cast<const float4*>(normals), mask, H, W, cth, fx, fy,
                                               cx, cy, persp ? 1 : 0, 0, parent, st);
   const long long nb = (long long)nbx * H + (long long)nby * W;
   const int cap = sms * 8;

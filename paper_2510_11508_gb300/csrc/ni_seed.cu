@@ -20,8 +20,8 @@
 //                  raster order, K = number of roots.
 #include "ni_internal.cuh"
 
-#define TSW 32
-#define TSH 16
+#define TSW NI_SEED_TSW
+#define TSH NI_SEED_TSH
 
 __device__ __forceinline__ bool seed_keep(const float4 a, const float4 b, double cth) {
   double d = __dadd_rn(__dmul_rn((double)a.x, (double)b.x), __dmul_rn((double)a.y, (double)b.y));

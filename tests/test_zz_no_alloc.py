@@ -70,6 +70,19 @@ def test_noalloc_same_map_twice_and_ragged():
         np.testing.assert_array_equal(got, ref)
 
 
+def test_noalloc_at_its_pixel_limit():
+    """The full 2048x2048 map holds exactly 2^22 pixels: the parent array
+    fills the static scratch to its last byte."""
+    w = make_workload("c3")
+    assert w.mask.size == 1 << 22
+    n, m = _inputs(w)
+    ref, Kr = _regular(n, m, w.camera, w.params["theta_c_deg"])
+    for _ in range(2):
+        got, K = _noalloc(n, m, w.camera, w.params["theta_c_deg"])
+        assert K == Kr
+        np.testing.assert_array_equal(got, ref)
+
+
 def test_noalloc_rejects_maps_beyond_its_scratch():
     L = ni.load()
     cam = ni.Camera(1, 100.0, 100.0, 0.0, 0.0)
