@@ -39,3 +39,38 @@ def rel_depth_error(z, zref, mask, camera):
         return O.aligned_rel_rmse(np.where(m, np.exp(z), np.nan), np.where(m, np.exp(zref), np.nan), mask,
                                   O.PERSP)
     return O.aligned_rel_rmse(np.where(m, z, np.nan), np.where(m, zref, np.nan), mask, O.ORTHO)
+
+
+# Per-pixel bound beside every RMSE bound: after the same island alignment, no
+# pixel's relative depth error (perspective) or range-relative error
+# (orthographic) may exceed this, so a small component with a wrong scale
+# cannot hide inside a small RMSE.
+PIXEL_TOL = 1e-3
+
+
+def rel_depth_max(z, zref, mask, camera):
+    """Largest per-pixel relative depth error of log-depth (or orthographic
+    depth) z against zref after the island-wise alignment of rel_depth_error:
+    max |s* e^z - e^zref| / e^zref (perspective) or max |z + o* - zref| /
+    (max - min of zref) (orthographic)."""
+    isl, n = O.islands(mask)
+    m = isl >= 0
+    if not m.any():
+        return 0.0
+    z = np.asarray(z, np.float64)
+    zr = np.asarray(zref, np.float64)
+    if camera == O.PERSP:
+        z, zr = np.exp(np.where(m, z, 0.0)), np.exp(np.where(m, zr, 0.0))
+    worst = 0.0
+    for i in range(n):
+        s = isl == i
+        if camera == O.PERSP:
+            den = np.sum(z[s] * z[s])
+            al = z[s] * (np.sum(z[s] * zr[s]) / den if den > 0 else 1.0)
+            worst = max(worst, float(np.max(np.abs(al - zr[s]) / np.abs(zr[s]))))
+        else:
+            al = z[s] + np.mean(zr[s] - z[s])
+            worst = max(worst, float(np.max(np.abs(al - zr[s]))))
+    if camera != O.PERSP:
+        worst /= max(float(np.ptp(zr[m])), 1e-300)
+    return worst

@@ -6,7 +6,7 @@ import torch
 import oracle as O
 from synth import make_workload
 
-from gpu_util import dev, integrator, rel_depth_error
+from gpu_util import PIXEL_TOL, dev, integrator, rel_depth_error, rel_depth_max
 
 pytestmark = pytest.mark.gpu
 
@@ -29,13 +29,15 @@ def test_integrate_matches_oracle(name, precond):
     zg = np.log(depth) if w.camera["camera"] == 1 else depth
     zr = np.nan_to_num(ref["z"])
     err = rel_depth_error(np.nan_to_num(zg), zr, w.mask, w.camera["camera"])
+    mx = rel_depth_max(np.nan_to_num(zg), zr, w.mask, w.camera["camera"])
     print(name, "stats", {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "merges")},
-          "oracle K0", ref["K0"], "K", ref["K"], "iters", ref["iters"], "err", err)
+          "oracle K0", ref["K0"], "K", ref["K"], "iters", ref["iters"], "err", err, "max", mx)
     assert st["K0"] == ref["K0"]
     assert np.isnan(depth[w.mask == 0]).all()
     if st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]:
         np.testing.assert_array_equal(labels, ref["labels"])
         assert err <= 1e-4
+        assert mx <= PIXEL_TOL
     else:
         pytest.fail(f"partition or iteration count differs: {st} vs oracle K={ref['K']} iters={ref['iters']}")
 
@@ -70,12 +72,14 @@ def test_full_size_c3(precond):
     ref = _C3_REF["ref"]
     depth, labels = depth.cpu().numpy(), labels.cpu().numpy()
     err = rel_depth_error(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
-    print("c3 precond", precond, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "ms_fill", "ms_total")},
+    mx = rel_depth_max(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
+    print("c3 precond", precond, "max", mx, {k: st[k] for k in ("K0", "K_final", "scale_iters", "fill_iters", "ms_fill", "ms_total")},
           "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
     assert st["K0"] == ref["K0"]
     assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
     np.testing.assert_array_equal(labels, ref["labels"])
     assert err <= 1e-4
+    assert mx <= PIXEL_TOL
 
 
 @pytest.mark.parametrize("name", ["c1", "c2"])
@@ -85,12 +89,14 @@ def test_pixel_level_limit_matches_oracle(name):
     w, depth, labels, st, ref = _run(name, theta_c_deg=None)
     zg = np.log(depth) if w.camera["camera"] == 1 else depth
     err = rel_depth_error(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, w.camera["camera"])
-    print(name, "pixel level", {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges", "ms_scale")},
+    mx = rel_depth_max(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, w.camera["camera"])
+    print(name, "pixel level", "max", mx, {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges", "ms_scale")},
           "oracle", ref["K0"], ref["K"], ref["iters"], "err", err)
     assert st["K0"] == int(w.mask.sum()) == ref["K0"]
     assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
     np.testing.assert_array_equal(labels, ref["labels"])
     assert err <= 1e-4
+    assert mx <= PIXEL_TOL
 
 
 @pytest.mark.parametrize("over", [dict(hard_outliers=True), dict(L=1e-6), dict(L=1e-4, U=1e-2)],
@@ -100,8 +106,10 @@ def test_outlier_variants_match_oracle(over):
     threshold and other (L, U) of Eq. 11."""
     w, depth, labels, st, ref = _run("c3_small", **over)
     err = rel_depth_error(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
-    print(over, {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges")}, "oracle", ref["K"], ref["iters"],
+    mx = rel_depth_max(np.nan_to_num(np.log(depth)), np.nan_to_num(ref["z"]), w.mask, 1)
+    print(over, "max", mx, {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges")}, "oracle", ref["K"], ref["iters"],
           "err", err)
     assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
     np.testing.assert_array_equal(labels, ref["labels"])
     assert err <= 1e-4
+    assert mx <= PIXEL_TOL

@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 from synth import generators as G, make_workload
 
-from gpu_util import dev, integrator, island_rms
+from gpu_util import PIXEL_TOL, dev, integrator, island_rms
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,7 @@ def test_fill_matches_oracle(name, batched, precision):
     rms = float(np.sqrt(np.mean(d * d))) / scale
     print(f"{name} batched={batched} prec={precision} K={K} fill rms={rms:.3e} max={np.abs(d).max():.3e}")
     assert rms <= TOL[precision]
+    assert float(np.abs(d).max()) / scale <= PIXEL_TOL
 
 
 @pytest.mark.parametrize("batched", [0, 1])
@@ -64,6 +65,7 @@ def test_fill_random_ragged_with_holes():
     z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=0)
     d = (z - zr)[mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
+    assert float(np.abs(d).max()) <= PIXEL_TOL
 
 
 def test_fill_irls_sweeps():
@@ -72,6 +74,7 @@ def test_fill_irls_sweeps():
     z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1, precond=0)
     d = (z - zr)[w.mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
+    assert float(np.abs(d).max()) <= PIXEL_TOL
 
 
 # ---- multigrid-preconditioned batched fill (precond = 1): same answer, fewer iterations
@@ -91,6 +94,7 @@ def test_fill_multigrid_matches_oracle(name, precision, fill_kernels):
     rms = float(np.sqrt(np.mean(d * d))) / scale
     print(f"{name} multigrid prec={precision} K={K} fill rms={rms:.3e} max={np.abs(d).max():.3e}")
     assert rms <= TOL[precision]
+    assert float(np.abs(d).max()) / scale <= PIXEL_TOL
 
 
 def test_fill_multigrid_exact_plane():
@@ -109,6 +113,7 @@ def test_fill_multigrid_ragged_shapes(H, W, fill_kernels):
     z, zr, K = _fill_pair(nrm, mask, cam, {"theta_c_deg": 3.0}, batched=1, precond=1, fill_kernels=fill_kernels)
     d = (z - zr)[mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4 if d.size else True
+    assert float(np.abs(d).max()) <= PIXEL_TOL if d.size else True
 
 
 def test_fill_multigrid_irls_sweeps():
@@ -117,6 +122,7 @@ def test_fill_multigrid_irls_sweeps():
     z, zr, K = _fill_pair(w.normals, w.mask, w.camera, p, batched=1, precond=1)
     d = (z - zr)[w.mask > 0]
     assert np.sqrt(np.mean(d * d)) < 1e-4
+    assert float(np.abs(d).max()) <= PIXEL_TOL
 
 
 def test_multigrid_needs_fewer_iterations():
@@ -156,3 +162,4 @@ def test_multigrid_mean_projection_option(name):
     d = (z - zr)[w.mask > 0]
     scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[w.mask > 0]))
     assert float(np.sqrt(np.mean(d * d))) / scale <= 1e-4
+    assert float(np.abs(d).max()) / scale <= PIXEL_TOL

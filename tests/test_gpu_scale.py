@@ -7,7 +7,7 @@ import pytest
 import oracle as O
 from synth import make_workload
 
-from gpu_util import dev, integrator, rel_depth_error
+from gpu_util import PIXEL_TOL, dev, integrator, rel_depth_error, rel_depth_max
 
 pytestmark = pytest.mark.gpu
 
@@ -27,8 +27,10 @@ def test_scale_loop_matches_oracle(name, T, use_graph):
     ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(p))
     zr = np.nan_to_num(ref["z"])
     err = rel_depth_error(z.cpu().numpy(), zr, w.mask, w.camera["camera"])
-    print(name, "graph", use_graph, "rel depth err", err, "E gpu", E[:4], "E ref", ref["energies"][:4])
+    mx = rel_depth_max(z.cpu().numpy(), zr, w.mask, w.camera["camera"])
+    print(name, "graph", use_graph, "rel depth err", err, "max", mx, "E gpu", E[:4], "E ref", ref["energies"][:4])
     assert err <= 1e-4
+    assert mx <= PIXEL_TOL
     np.testing.assert_allclose(E, ref["energies"], rtol=5e-3, atol=1e-9 * max(ref["energies"]))
 
 
