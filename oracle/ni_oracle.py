@@ -313,6 +313,50 @@ def project_zero_mean(x, block, nblocks):
     return x - mean[block]
 
 
+# Blocks above this many nodes are solved by CG instead of sparse LU (the LU's
+# fill-in of a grid Laplacian of a few million nodes exceeds host memory).
+LU_MAX_NODES = 1_500_000
+CG_RTOL = 1e-12
+
+
+def cg_min_norm(M, g, rtol=CG_RTOL, maxiter=None):
+    """cg(M, g) from x = 0 (Eq. 10 / Eq. 14 as the paper states them) on one
+    connected, singular Laplacian block: Jacobi-preconditioned conjugate
+    gradients in float64 until ||g - M x|| <= rtol ||g||, then the block's mean
+    removed.  g is first projected onto the range of M (zero sum), which CG from
+    0 would otherwise carry as a constant drift.  Returns (x, iterations)."""
+    M = sp.csr_matrix(M)
+    g = np.asarray(g, np.float64)
+    g = g - g.mean()
+    n = M.shape[0]
+    d = M.diagonal()
+    inv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    x = np.zeros(n)
+    r = g.copy()
+    gn = float(np.linalg.norm(g))
+    if gn == 0.0:
+        return x, 0
+    z = inv * r
+    p = z.copy()
+    rz = float(r @ z)
+    it = 0
+    for it in range(1, (maxiter or 20 * n) + 1):
+        q = M @ p
+        pq = float(p @ q)
+        if pq <= 0.0:
+            break
+        alpha = rz / pq
+        x += alpha * p
+        r -= alpha * q
+        if np.linalg.norm(r) <= rtol * gn:
+            break
+        z = inv * r
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x - x.mean(), it
+
+
 def solve_min_norm(M, g):
     """Minimum-norm solution of the singular normal equations M x = g of a
     weighted graph Laplacian M (the result cg(M, g) approaches from x = 0).
@@ -321,7 +365,9 @@ def solve_min_norm(M, g):
     M's graph (off-diagonal entries != 0) one node is pinned to 0, the remaining
     nonsingular system is solved by sparse LU (scipy's spsolve), and the block's
     mean is removed (the null space of a connected Laplacian block is the
-    constants).  Isolated nodes get 0.  Returns x."""
+    constants).  Isolated nodes get 0.  Blocks of more than LU_MAX_NODES nodes
+    are solved by `cg_min_norm` instead (the CG the paper names, to a relative
+    residual of 1e-12).  Returns x."""
     from scipy.sparse.linalg import spsolve
     M = sp.csr_matrix(M)
     n = M.shape[0]
@@ -340,6 +386,9 @@ def solve_min_norm(M, g):
     for c in range(nb):
         b0, b1 = bounds[c], bounds[c + 1]
         if b1 - b0 < 2:
+            continue
+        if b1 - b0 > LU_MAX_NODES:
+            xp[b0:b1] = cg_min_norm(Mp[b0:b1, b0:b1], gp[b0:b1])[0]
             continue
         # pin the block's first node (its smallest index) to 0
         Mk = Mp[b0 + 1:b1, b0 + 1:b1].tocsc()
@@ -426,6 +475,82 @@ def fill_components(geo: Geometry, labels, K, k=2.0, n_irls=1):
     out = np.full(n, np.nan)
     out[vidx] = zt[vidx]
     return out, iters
+
+
+def _fill_crops(task):
+    """Worker of fill_components_by_crops: the fill of each component of the
+    task on the crop of its bounding box, every pixel outside the component
+    masked out and the principal point shifted by the crop's offset.
+    Returns [(component, v0, u0, crop mask, z~ on the crop mask)]."""
+    cam_t, k, n_irls, conn, items = task
+    cam = Camera(*cam_t)
+    out = []
+    for c, v0, u0, ncrop, m in items:
+        cc = Camera(cam.camera, cam.fx, cam.fy, cam.cx - u0, cam.cy - v0)
+        geo = geometry(ncrop, m.astype(np.uint8), cc, conn)
+        lab = np.where(m.reshape(-1), 0, -1).astype(np.int64)
+        z, _ = fill_components(geo, lab, 1, k, n_irls)
+        out.append((c, v0, u0, m, z.reshape(m.shape)[m]))
+    return out
+
+
+def fill_components_by_crops(normals, mask, cam: Camera, labels, K, k=2.0, n_irls=1, conn=4, workers=1,
+                             task_px=1 << 21):
+    """The fill of Sec. 3.3 solved component by component, as the paper does
+    (its components are filled independently, in parallel processes).
+
+    A component's block of the block-diagonal system involves only its own
+    pixels and intra-component edges, and every quantity of Eqs. 3-6 on those
+    edges depends only on the two pixels' normals and ray directions.  So the
+    block equals `fill_components` run on the crop of the component's bounding
+    box with every other pixel masked out and (c_x, c_y) shifted by the crop's
+    offset (integer shifts: the ray directions are the same numbers).  The
+    opposite neighbour -b then counts only inside the component, which is the
+    fill's reading of Eq. 4.  `workers` > 1 spreads the components over a
+    spawn process pool.  Returns (z~ [H*W], NaN at invalid pixels; 1 sweep
+    count as fill_components)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    H, W = mask.shape
+    lab = np.asarray(labels).reshape(H, W)
+    nrm = np.asarray(normals).reshape(H, W, -1)
+    vv, uu = np.nonzero(lab >= 0)
+    cl = lab[vv, uu]
+    big = np.iinfo(np.int64).max
+    v0 = np.full(K, big); v1 = np.full(K, -1); u0 = np.full(K, big); u1 = np.full(K, -1)
+    np.minimum.at(v0, cl, vv); np.maximum.at(v1, cl, vv)
+    np.minimum.at(u0, cl, uu); np.maximum.at(u1, cl, uu)
+    size = np.bincount(cl, minlength=K)
+    cam_t = (cam.camera, cam.fx, cam.fy, cam.cx, cam.cy)
+    tasks, cur, cur_px = [], [], 0
+    for c in np.argsort(-size, kind="stable"):
+        c = int(c)
+        if size[c] == 0:
+            continue
+        sl = (slice(int(v0[c]), int(v1[c]) + 1), slice(int(u0[c]), int(u1[c]) + 1))
+        m = lab[sl] == c
+        cur.append((c, int(v0[c]), int(u0[c]), np.ascontiguousarray(nrm[sl]), m))
+        cur_px += m.size
+        if cur_px >= task_px:
+            tasks.append((cam_t, k, n_irls, conn, cur)); cur, cur_px = [], 0
+    if cur:
+        tasks.append((cam_t, k, n_irls, conn, cur))
+    zt = np.full(H * W, np.nan)
+    zt2 = zt.reshape(H, W)
+
+    def put(res):
+        for c, a0, b0, m, z in res:
+            blk = zt2[a0:a0 + m.shape[0], b0:b0 + m.shape[1]]
+            blk[m] = z
+
+    if workers <= 1 or len(tasks) <= 1:
+        for t in tasks:
+            put(_fill_crops(t))
+    else:
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            for res in ex.map(_fill_crops, tasks):
+                put(res)
+    return zt, max(1, n_irls)
 
 
 # ---------------------------------------------------------------------------
@@ -599,21 +724,28 @@ def scale_loop(geo: Geometry, labels, K, zt, params: Params, record=False):
                 energies=[E[i] for i in range(1, t + 1)], iters=t, merges=merges, steps=steps)
 
 
-def integrate(normals, mask, cam, params, record=False):
+def integrate(normals, mask, cam, params, record=False, workers=0):
     """Algorithm 1 end to end: seeding (Sec. 3.3), fill (Eqs. 9-10), then the
     relative-scale loop with optional merging (Sec. 3.4-3.5).  Returns a dict
     with z (log-depth, or depth for the orthographic reading, [H, W], NaN
     invalid), depth (exp(z) for perspective), labels0/K0 after seeding, the
-    final labels/K, the energies E_1..E_t and the iteration count."""
+    final labels/K, the energies E_1..E_t and the iteration count.
+    workers = 0 fills all components in one block-diagonal solve
+    (`fill_components`); workers >= 1 fills them one by one on their crops
+    (`fill_components_by_crops`) in that many processes."""
     if isinstance(cam, dict):
         cam = Camera.from_dict(cam)
     if isinstance(params, dict):
         params = Params.from_dict(params)
     mask = np.asarray(mask).astype(np.uint8)
     H, W = mask.shape
-    geo = geometry(normals, mask, cam, params.connectivity)
     labels, K = seed_components(normals, mask, params.theta_c_deg, params.connectivity)
-    zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls)
+    if workers >= 1:
+        zt, fill_iters = fill_components_by_crops(normals, mask, cam, labels, K, params.k, params.n_fill_irls,
+                                                  params.connectivity, workers)
+    geo = geometry(normals, mask, cam, params.connectivity)
+    if workers < 1:
+        zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls)
     r = scale_loop(geo, labels, K, zt, params, record)
     out = r["z"].reshape(H, W)
     depth = np.exp(out) if cam.camera == PERSP else out
