@@ -70,9 +70,9 @@ typedef struct {
   double theta_c_deg;       /* seeding threshold theta_c (Sec. 3.3); < 0 = None (one
                                component per pixel, the paper's pixel-level limit) */
   int connectivity;         /* 4 (default) or 8 (H * W < 2^29, batched = 0): pixel
-                               graph of every stage.  With 8, the stages after the
-                               seeding are not yet enabled: ni_solve_components and
-                               ni_integrate* return NI_ERR_INVALID_ARG */
+                               graph of every stage (8 adds the lower-right and
+                               lower-left edges; the fill then runs the plain
+                               PCG with a 9-point stencil) */
   double k;                 /* sigmoid sharpness of the BiNI weight (Sec. 3.1), default 2 */
   double L, U;              /* outlier thresholds of Eq. 11, default 1e-5, 1e-3 */
   int T;                    /* maximum relative-scale iterations, default 15 */
@@ -108,6 +108,11 @@ typedef struct {
   int fill_kernels;         /* multigrid fill: 0 one kernel per pass, chunks of iterations
                                replayed from a CUDA graph; 1 (default) one persistent
                                cooperative kernel with software grid barriers */
+  int scale_solver;         /* relative-scale PCG launch: 0 (default) chosen by the number of
+                               components, 1 one thread-block cluster of up to 16 CTAs
+                               (hardware cluster barriers, reductions through distributed
+                               shared memory), 2 one CTA or a cooperative grid with
+                               software barriers */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */
@@ -130,6 +135,7 @@ typedef struct {
   int32_t warm_fallbacks;   /* components whose energy-optimal warm-start scale was 0 (cold start) */
   int32_t fill_fallbacks;   /* components the multigrid PCG left above the tolerance after 2000
                                iterations, finished by the Jacobi PCG */
+  int64_t scale_cg_total;   /* scale-PCG iterations summed over the loop's solves */
 } ni_stats;
 
 /* Default configuration for an H x W map (Algorithm 1's defaults of the paper's

@@ -100,6 +100,7 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->ctas_per_sm < 0 || c->ctas_per_sm > 8) { why = "ctas_per_sm in [0, 8]"; return NI_ERR_INVALID_ARG; }
   if (c->mg_coarse_sweeps < 0 || c->mg_coarse_sweeps > 64) { why = "mg_coarse_sweeps in [0, 64]"; return NI_ERR_INVALID_ARG; }
   if (c->fill_kernels != 0 && c->fill_kernels != 1) { why = "fill_kernels must be 0 or 1"; return NI_ERR_INVALID_ARG; }
+  if (c->scale_solver < 0 || c->scale_solver > 2) { why = "scale_solver must be 0, 1 or 2"; return NI_ERR_INVALID_ARG; }
   if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;
@@ -131,7 +132,7 @@ ni_status ensure_component_capacity(ni_handle* h, int K) {
   if (e == cudaSuccess) e = dalloc(&h->kparent, k);
   if (e == cudaSuccess) e = dalloc(&h->kmap, k);
   if (e == cudaSuccess) e = dalloc(&h->kkey, k);
-  if (e == cudaSuccess) e = dalloc(&h->sv, 7 * k);
+  if (e == cudaSuccess) e = dalloc(&h->sv, 11 * k);
   if (e == cudaSuccess) e = dalloc(&h->sd, k);
   if (e == cudaSuccess) e = dalloc(&h->row_ptr, k + 1);
   if (e != cudaSuccess) {
@@ -324,17 +325,8 @@ extern "C" ni_status ni_seed_components(ni_handle* h, const float* normals, cons
   return ni_cuda_check(h, cudaStreamSynchronize(s), "seeding");
 }
 
-// The fill, relative-scale loop and merging are built for 4-connectivity; with
-// 8-connectivity the handle seeds only.
-static ni_status need_conn4(ni_handle* h) {
-  if (h->cfg.connectivity == 4) return NI_OK;
-  return ni_fail(h, NI_ERR_INVALID_ARG, "8-connectivity covers the seeding only: the fill, scale loop and "
-                                        "merging need connectivity = 4");
-}
-
 extern "C" ni_status ni_solve_components(ni_handle* h, float* logdepth_out, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
-  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (h->stage < 1) return ni_fail(h, NI_ERR_STATE, "ni_solve_components before ni_seed_components");
   if (h->cfg.warm_start && !h->net)
     return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
@@ -477,7 +469,6 @@ extern "C" ni_status ni_merge_residuals(ni_handle* h, const float* chi_abs, int3
 extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint8_t* mask, float* depth_out,
                                   int32_t* labels_out, ni_stats* stats, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
-  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (!depth_out) return ni_fail(h, NI_ERR_INVALID_ARG, "depth_out is required");
   cudaStream_t s = (cudaStream_t)stream;
   const long long launches0 = h->launches;
@@ -523,6 +514,7 @@ extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint
     stats->kernel_launches = h->launches - launches0;
     stats->warm_fallbacks = d->warm_fallbacks;
     stats->fill_fallbacks = h->fill_fallbacks;
+    stats->scale_cg_total = (int64_t)d->scale_cg_total;
   }
   if (fill_rc != NI_OK) return ni_fail(h, fill_rc, fill_msg);
   return NI_OK;
@@ -531,7 +523,6 @@ extern "C" ni_status ni_integrate(ni_handle* h, const float* normals, const uint
 extern "C" ni_status ni_integrate_host(ni_handle* h, const float* normals_host, const uint8_t* mask_host,
                                        float* depth_host, ni_stats* stats, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
-  if (need_conn4(h) != NI_OK) return NI_ERR_INVALID_ARG;
   if (!normals_host || !mask_host || !depth_host) return ni_fail(h, NI_ERR_INVALID_ARG, "null host buffer");
   cudaStream_t s = (cudaStream_t)stream;
   const size_t N = (size_t)h->N;

@@ -1,6 +1,6 @@
 """Seeding with 8-connectivity (the pixel graph of the paper's DiLiGenT
 experiments and of its connectivity ablation): GPU labels and K equal the
-oracle's bit for bit; the later stages refuse connectivity 8."""
+oracle's bit for bit."""
 import math
 
 import numpy as np
@@ -80,16 +80,3 @@ def test_full_size_c3_labels_8():
     w = make_workload("c3")
     K = _check(w.normals, w.mask, w.camera, w.params["theta_c_deg"])
     print("c3 K0 8-connected =", K)
-
-
-def test_later_stages_refuse_connectivity_8():
-    w = make_workload("c1")
-    H, W = w.mask.shape
-    n, m = dev(w.normals, w.mask)
-    it = integrator(H, W, w.camera, w.params, connectivity=8, batched=0)
-    it.seed_components(n, m)
-    with pytest.raises(ni.NIError) as ei:
-        it.solve_components()
-    assert ei.value.status == 1
-    with pytest.raises(ni.NIError):
-        it.integrate(n, m)
