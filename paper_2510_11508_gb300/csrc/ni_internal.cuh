@@ -56,6 +56,7 @@ struct DevState {
   int n_valid;     // valid pixels of the map
   int warm_fallbacks;  // components whose warm start was scaled to zero (cold start)
   unsigned long long fill_px_iters;  // sum over components of size x PCG iterations
+  unsigned long long scale_cg_total; // scale-PCG iterations summed over the loop
   double E[NI_MAX_T + 1];  // E[0] = eps, E[t] after iteration t
   double cg[8];            // plain fill PCG scalars
   GridBar bar;             // software grid barrier of persistent kernels
@@ -75,6 +76,7 @@ struct ni_handle {
   ni_config cfg;
   int dev = 0;
   int num_sms = 0;
+  int scale_cluster = -1;      // CTAs of the cluster-mode scale PCG (-1 not yet queried, 0 unavailable)
   int H = 0, W = 0;
   int N = 0;
   int Npad = 0;                // N rounded up to a multiple of 1024 (allocation size)

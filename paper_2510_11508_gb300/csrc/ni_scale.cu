@@ -15,7 +15,9 @@
 //                  (W_{b->a} + W_{a->b}) W^out(|chi|), Eqs. 5, 11), reduced per
 //                  pair into (w_p, h_p = sum w chi oriented lo -> hi, q_p = sum w chi^2);
 //   k_node_assemble diagonal and right-hand side of A_m^T W A_m s = A_m^T W b_m (Eq. 14);
-//   k_scale_cg     Jacobi-PCG in float64, then E_t (energy of the system just
+//   k_scale_cg     Jacobi-PCG in float64 (single-reduction form, exact
+//                  fixed-point inner products; one thread-block cluster or a
+//                  cooperative grid), then E_t (energy of the system just
 //                  solved), the stop test, and the update of Eqs. 7-8 applied to
 //                  a per-component float64 offset (z~_a = x_a + soff[pi(a)]), so
 //                  the per-pixel log-depth is only touched when merging.
@@ -533,11 +535,12 @@ __global__ void k_edge_accum(EdgeArgs A) {
   }
 }
 
-// Also gabs_c = sum |h_p|: the size of the terms that cancel in g_c, which sets
-// the rounding floor of the right-hand side.
+// Writes the inverse of the Jacobi diagonal.  Also gabs_c = sum |h_p|: the size
+// of the terms that cancel in g_c, which sets the rounding floor of the
+// right-hand side.
 __global__ void k_node_assemble(const int* __restrict__ row_ptr, const int* __restrict__ csr_pair,
                                 const int* __restrict__ p_lo, const double* __restrict__ p_acc,
-                                DevState* st, double* __restrict__ diag, double* __restrict__ g,
+                                DevState* st, double* __restrict__ invd, double* __restrict__ g,
                                 double* __restrict__ gabs, double* __restrict__ csr_w) {
   if (st->converged) return;
   const int K = st->K;
@@ -558,7 +561,7 @@ __global__ void k_node_assemble(const int* __restrict__ row_ptr, const int* __re
     gs = warp_sum_d(gs);
     ga = warp_sum_d(ga);
     if (lane == 0) {
-      diag[c] = d;
+      invd[c] = d > 0.0 ? 1.0 / d : 0.0;   // one FP64 division per component and iteration
       g[c] = gs;
       gabs[c] = ga;
     }
@@ -574,205 +577,579 @@ struct ScaleArgs {
   const int* p_lo;
   const int* p_hi;
   const double* p_acc;
-  double* diag;        // the Jacobi diagonal; replaced by its inverse at the start of the solve
+  const double* invd;  // inverse Jacobi diagonal (0 for a row without entries)
   const double* g;
   const double* gabs;
-  double* s;
-  double* r;
-  double* z;
-  double* pp;
-  double* qq;
-  double* red;    // 3 slots x 4 doubles
+  double* x;           // the solution s~ of Eq. 14
+  double* p;           // search direction
+  double* r[2];        // residual
+  double* q[2];        // q = L p
+  double* w[2];        // w = L u, u = D^-1 r
+  double* u;           // cluster mode: u of every row, read by the neighbouring rows
+  long long* red;      // grid mode: per-CTA partial sums, 2 slots x gridDim x 4 x (q, e)
   double* soff;
   double tol2;
   int maxit;
   int T;
   double dE_max;
+  int smem_bytes;      // dynamic shared memory of the launch (CSR cache)
 };
 
-// CTA sum of three values, the same additions as three block_sum_d calls.  A
-// warp whose values are all zero (its rows lie past the last component) or sit
-// in lane 0 alone (a long row's result) skips its shuffle trees, which are most
-// of the FP64 instructions of an iteration when K is small against the CTA.
-__device__ __forceinline__ void block_sum3_d(double& a, double& b, double& c, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  const unsigned m = __ballot_sync(NI_FULL, a != 0.0 || b != 0.0 || c != 0.0);
-  if (m & ~1u) {
-    a = warp_sum_d(a);
-    b = warp_sum_d(b);
-    c = warp_sum_d(c);
+// ---- exact sums.  FP64 issues at about 2 lanes per clock per SM on this part
+// (a dependent FP64 add or FMA waits 64 cycles), so a shuffle tree of FP64
+// additions costs 64 cycles a level per value.  Sums here are taken in 64-bit
+// fixed point: a warp finds the largest exponent E of its terms (an integer
+// max), turns every term into an integer multiple of 2^(E - 1022 - S) and adds
+// the integers exactly; warps, CTAs and the cluster or grid then combine their
+// (integer, exponent) pairs by aligning them to the largest exponent with an
+// integer shift.  One conversion back to FP64 at the end.  S = 62 - ceil(log2
+// of the number of terms), so no integer sum can overflow.  Each term and each
+// alignment is rounded to the grain 2^(E - 1022 - S), 2^-S of the largest
+// term.  The result does not depend on the order of the terms or on which warp
+// adds what: every CTA of a grid or cluster that combines the same partials
+// holds the same bits.
+struct Fx {
+  long long q;   // value q 2^(e - 1022 - S); e = 0: zero, e = 2047: not finite
+  int e;
+};
+
+__device__ __forceinline__ int fx_exp(double x) {   // biased exponent; subnormal 1, zero 0, inf/nan 2047
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  const int e = (int)(b >> 52);
+  return (e == 0 && b != 0ull) ? 1 : e;
+}
+
+// x 2^(S - (E - 1022)) rounded to the nearest integer; requires fx_exp(x) <= E < 2047
+__device__ __forceinline__ long long fx_quant(double x, int E, int S) {
+  const long long bits = __double_as_longlong(x);
+  const unsigned long long b = (unsigned long long)bits & 0x7fffffffffffffffull;
+  int e = (int)(b >> 52);
+  unsigned long long m = b & 0xfffffffffffffull;
+  if (e == 0) {
+    if (m == 0ull) return 0;
+    e = 1;
+  } else {
+    m |= 0x10000000000000ull;   // x = m 2^(e - 1075)
   }
-  __syncthreads();
-  if (lane == 0) {
-    sh[3 * wid] = a;
-    sh[3 * wid + 1] = b;
-    sh[3 * wid + 2] = c;
+  const int sh = e - E + S - 53;   // <= S - 53 <= 9
+  long long q;
+  if (sh >= 0) q = (long long)(m << sh);
+  else if (sh > -62) q = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+  else q = 0;
+  return bits < 0 ? -q : q;
+}
+
+// q 2^-de rounded (de >= 0); |q| < 2^62
+__device__ __forceinline__ long long fx_shift(long long q, int de) {
+  if (de == 0) return q;
+  if (de > 62) return 0;
+  return (q + (1ll << (de - 1))) >> de;
+}
+
+__device__ __forceinline__ double fx_double(Fx a, int S) {
+  if (a.e == 0) return 0.0;
+  if (a.e == 2047) return __longlong_as_double(0x7ff8000000000000ll);
+  return scalbn((double)a.q, a.e - 1022 - S);
+}
+
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(NI_FULL, v, o));
+  return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(NI_FULL, v, o);
+  return v;
+}
+
+// the terms of the 32 lanes -> one Fx, in every lane
+__device__ __forceinline__ Fx warp_fx(double v, int S) {
+  const int E = warp_max_i(fx_exp(v));
+  if (E == 0 || E == 2047) return Fx{0, E};
+  return Fx{warp_sum_ll(fx_quant(v, E, S)), E};
+}
+
+// the partials of the 32 lanes (Fx{0, 0} for none) -> one Fx, in every lane
+__device__ __forceinline__ Fx warp_fx_combine(Fx a) {
+  const int E = warp_max_i(a.e);
+  if (E == 0 || E == 2047) return Fx{0, E};
+  return Fx{warp_sum_ll(a.e == 0 ? 0ll : fx_shift(a.q, E - a.e)), E};
+}
+
+// CTA sum of NV values per thread; the result in every thread.
+// shq / she: 33 * NV entries of shared memory
+template <int NV>
+__device__ __forceinline__ void block_fx(const double (&v)[NV], Fx (&out)[NV], int S, long long* shq, int* she) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const Fx f = warp_fx(v[k], S);
+    if (lane == 0) {
+      shq[wid * NV + k] = f.q;
+      she[wid * NV + k] = f.e;
+    }
   }
   __syncthreads();
   if (wid == 0) {
-    double x = lane < nw ? sh[3 * lane] : 0.0, y = lane < nw ? sh[3 * lane + 1] : 0.0,
-           z = lane < nw ? sh[3 * lane + 2] : 0.0;
-    x = warp_sum_d(x);
-    y = warp_sum_d(y);
-    z = warp_sum_d(z);
-    if (lane == 0) {
-      sh[96] = x;
-      sh[97] = y;
-      sh[98] = z;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const Fx f = warp_fx_combine(lane < nw ? Fx{shq[lane * NV + k], she[lane * NV + k]} : Fx{0, 0});
+      if (lane == 0) {
+        shq[32 * NV + k] = f.q;
+        she[32 * NV + k] = f.e;
+      }
     }
   }
   __syncthreads();
-  a = sh[96];
-  b = sh[97];
-  c = sh[98];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = Fx{shq[32 * NV + k], she[32 * NV + k]};
 }
 
-// Grid-wide sum of three values.  gridDim 1: a block reduction.  Otherwise
-// partial sums go to rotating slots (slot m % 3 at call m; block 0 clears slot
-// (m + 1) % 3, last read two calls ago) followed by a bounded grid barrier.
-__device__ __forceinline__ bool grid_sum3(double& a, double& b, double& c, double* red, int& ncall,
-                                          DevState* st, double* sh) {
-  double ba = a, bb = b, bc = c;
-  block_sum3_d(ba, bb, bc, sh);
-  if (gridDim.x == 1) {
-    a = ba; b = bb; c = bc;
-    return true;
-  }
-  double* R = red + 4 * (ncall % 3);
-  if (threadIdx.x == 0) {
-    if (blockIdx.x == 0) {
-      double* Z = red + 4 * ((ncall + 1) % 3);
-      Z[0] = 0.0; Z[1] = 0.0; Z[2] = 0.0;
+// ---- one thread-block cluster (MODE 1): a single cluster of up to 16 CTAs on
+// as many SMs; the FP64 work is spread over them and synchronisation is the
+// hardware cluster barrier.  A cluster-wide sum: every CTA publishes its
+// partial in its own shared memory, a cluster barrier, then warp 0 of every
+// CTA reads all partials through distributed shared memory and combines them.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned cluster_ctas() {
+  unsigned n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
+}
+
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ long long dsmem_ld_s64(const long long* p, unsigned rank) {
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(dsmem_addr(p, rank)) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int dsmem_ld_s32(const int* p, unsigned rank) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(p, rank)) : "memory");
+  return v;
+}
+
+struct RedShared {
+  long long q[33 * 4];
+  int e[33 * 4];
+  long long slot_q[2 * 4];   // cluster mode: this CTA's published partials, two slots used in turn
+  int slot_e[2 * 4];
+};
+
+// Sum over the cluster (MODE 1) or the grid (MODE 0; one CTA: the CTA sum);
+// the result in every thread.  A slot or global partial is rewritten two sums
+// later, after another barrier, when every CTA has read it.
+template <int MODE, int NV>
+__device__ __forceinline__ bool reduce_fx(const double (&v)[NV], Fx (&out)[NV], int S, RedShared& R,
+                                          long long* gred, int& ncall, DevState* st) {
+  block_fx<NV>(v, out, S, R.q, R.e);
+  if constexpr (MODE == 1) {
+    const int s4 = 4 * (ncall & 1);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        R.slot_q[s4 + k] = out[k].q;
+        R.slot_e[s4 + k] = out[k].e;
+      }
     }
-    if (ba != 0.0) atomicAdd(&R[0], ba);
-    if (bb != 0.0) atomicAdd(&R[1], bb);
-    if (bc != 0.0) atomicAdd(&R[2], bc);
+    ++ncall;
+    cluster_barrier();   // every thread of this CTA is also past its reads of the broadcast entries
+    if (threadIdx.x < 32) {
+      const unsigned lane = threadIdx.x, nc = cluster_ctas();
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        Fx a{0, 0};
+        if (lane < nc) a = Fx{dsmem_ld_s64(&R.slot_q[s4 + k], lane), dsmem_ld_s32(&R.slot_e[s4 + k], lane)};
+        const Fx f = warp_fx_combine(a);
+        if (lane == 0) {
+          R.q[32 * NV + k] = f.q;
+          R.e[32 * NV + k] = f.e;
+        }
+      }
+    }
+  } else {
+    if (gridDim.x == 1) return true;
+    const int nb = gridDim.x;
+    long long* G = gred + (size_t)(ncall & 1) * nb * 8;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        G[blockIdx.x * 8 + 2 * k] = out[k].q;
+        G[blockIdx.x * 8 + 2 * k + 1] = out[k].e;
+      }
+    }
+    ++ncall;
+    if (!grid_barrier(&st->bar, &st->err)) return false;
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        // fold this lane's CTAs (aligned to their largest exponent), then the lanes
+        int e = 0;
+        for (int b = lane; b < nb; b += 32) e = max(e, (int)__ldcg(&G[b * 8 + 2 * k + 1]));
+        long long q = 0;
+        if (e != 2047) {
+          for (int b = lane; b < nb; b += 32) {
+            const int eb = (int)__ldcg(&G[b * 8 + 2 * k + 1]);
+            if (eb != 0) q += fx_shift(__ldcg(&G[b * 8 + 2 * k]), e - eb);
+          }
+        }
+        const Fx f = warp_fx_combine(Fx{q, e});
+        if (lane == 0) {
+          R.q[32 * NV + k] = f.q;
+          R.e[32 * NV + k] = f.e;
+        }
+      }
+    }
   }
-  ncall++;
-  if (!grid_barrier(&st->bar, &st->err)) return false;
-  volatile double* VR = R;
-  a = VR[0]; b = VR[1]; c = VR[2];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = Fx{R.q[32 * NV + k], R.e[32 * NV + k]};
   return true;
 }
 
-__device__ __forceinline__ bool gsync(DevState* st) {
-  if (gridDim.x == 1) { __syncthreads(); return true; }
-  return grid_barrier(&st->bar, &st->err);
+// The rows a CTA owns are one contiguous range [lo, hi); thread t owns rows
+// lo + t + k blockDim.  The CTA's slice of the CSR (row pointers made local,
+// column indices, weights) is copied into shared memory when it fits.
+struct RowSlice {
+  int lo, hi, base;
+  bool cached;
+  const int* rp;      // local row pointers (cached) or the global ones
+  const int* col;
+  const double* wgt;
+};
+
+// w_c = sum_j w_cj (u_c - u_j) for the rows this thread owns, in a warp-uniform
+// traversal: a warp visits 32 consecutive rows together; rows of at most 32
+// entries take one thread, longer ones (the quotient graph's degrees follow the
+// component sizes: a large component borders hundreds of small ones) are then
+// done by the whole warp one after the other.  uj(j) gives u_j; row(c, u_c, w_c)
+// is called once per owned row c, by its owning thread, and returns the row's
+// three inner-product terms, summed into s0, s1, s2.
+struct Terms3 {
+  double a, b, c;
+};
+
+template <class UJ, class ROW>
+__device__ __forceinline__ void spmv_rows(const RowSlice& RS, UJ uj, ROW row, double& s0, double& s1, double& s2) {
+  const int lane = threadIdx.x & 31;
+  for (int c0 = RS.lo + threadIdx.x - lane; c0 < RS.hi; c0 += blockDim.x) {   // warp-uniform
+    const int c = c0 + lane;
+    const bool own = c < RS.hi;
+    int b = 0, e = 0;
+    double uc = 0.0;
+    if (own) {
+      const int i = RS.cached ? c - RS.lo : c;
+      b = RS.rp[i];
+      e = RS.rp[i + 1];
+      uc = uj(c);
+    }
+    const bool lng = e - b > 32;
+    double acc = 0.0;
+    if (own && !lng) {
+#pragma unroll 4
+      for (int j = b; j < e; ++j) acc += RS.wgt[j] * (uc - uj(RS.col[j]));
+    }
+    unsigned m = __ballot_sync(NI_FULL, lng);
+    while (m) {
+      const int l = __ffs(m) - 1;
+      m &= m - 1;
+      const int rb = __shfl_sync(NI_FULL, b, l), re = __shfl_sync(NI_FULL, e, l);
+      const double ur = __shfl_sync(NI_FULL, uc, l);
+      double a2 = 0.0;
+#pragma unroll 4
+      for (int j = rb + lane; j < re; j += 32) a2 += RS.wgt[j] * (ur - uj(RS.col[j]));
+      a2 = warp_sum_d(a2);
+      if (lane == l) acc = a2;
+    }
+    if (own) {
+      const Terms3 t = row(c, uc, acc);
+      s0 += t.a;
+      s1 += t.b;
+      s2 += t.c;
+    }
+  }
 }
 
-__global__ void __launch_bounds__(1024) k_scale_cg(ScaleArgs A) {
-  __shared__ double sh[99];
+// The relative-scale solve s~ <- cg(A^T W A, A^T W b) (Eq. 14) on the quotient
+// Laplacian L (CSR, FP64), Jacobi-preconditioned, from s~ = 0, in the
+// single-reduction form of Chronopoulos and Gear: with u = D^-1 r and w = L u,
+// one iteration is
+//   p = u + beta p,  q = w + beta q  (q = L p),  x += alpha p,  r -= alpha q,
+//   u = D^-1 r,  w = L u,  gamma = r.u,  delta = w.u,  rho = r.r,
+//   beta' = gamma' / gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha),
+// so the three inner products share one grid-wide sum.
+//   MODE 0 (one CTA or a cooperative grid): one pass per iteration.  Each row
+//     recomputes its neighbours' new u from their r, w and q of the previous
+//     iteration (the same FMAs their owners evaluate, so the same bits); r, q
+//     and w are double-buffered so no pass reads what it writes.
+//   MODE 1 (one cluster): two passes per iteration, the row updates (storing
+//     u) and then w = L u with the inner products, a cluster barrier between.
+// Thread 0 turns the sums into the scalars (two independent divisions an
+// iteration) and broadcasts them.
+template <int MODE>
+__global__ void __launch_bounds__(256, 1) k_scale_cg(ScaleArgs A) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ RedShared R;
+  __shared__ double sc[4];   // alpha, beta, done
   DevState* st = A.st;
   if (*(volatile int*)&st->converged) return;
   const int K = st->K, P = st->nP;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   int ncall = 0;
-  double rz = 0, ga2 = 0, gg = 0;
-  for (int c = tid; c < K; c += nthr) {
-    const double d = A.diag[c], rc = A.g[c];
-    const double id = d > 0.0 ? 1.0 / d : 0.0;   // one FP64 division per component and solve
-    A.diag[c] = id;
-    const double zc = rc * id;
-    A.s[c] = 0.0;
-    A.r[c] = rc;
-    A.z[c] = zc;
-    A.pp[c] = zc;
-    rz += rc * zc;
-    ga2 += A.gabs[c] * A.gabs[c];
-    gg += rc * rc;
-  }
-  if (!grid_sum3(rz, ga2, gg, A.red, ncall, st, sh)) return;
-  // stop at the relative tolerance, or once the residual is at the rounding
-  // level of the terms that cancel in g (a system that is already solved has a
-  // right-hand side made of rounding noise)
-  const double floor2 = (64.0 * 1.1102230246251565e-16) * (64.0 * 1.1102230246251565e-16) * ga2;
-  const double stop2 = fmax(A.tol2 * gg, floor2);
-  int it = 0;
-  bool done = !(gg > 0.0) || gg <= stop2;
-  // q = L p.  Rows of at most 32 entries take a thread each, longer rows a warp
-  // each: the quotient graph's degrees follow the component sizes (a large
-  // component borders thousands of small ones).  Entry weights come from csr_w.
-  const int lane = threadIdx.x & 31, wid = tid >> 5, nwarp = nthr >> 5;
-  while (!done && it < A.maxit) {
-    double pq = 0, d1 = 0, d2 = 0;
-    for (int c = tid; c < K; c += nthr) {
-      const int b = A.row_ptr[c], e = A.row_ptr[c + 1];
-      if (e - b > 32) continue;
-      const double pc = A.pp[c];
-      double acc = 0.0;
-#pragma unroll 4
-      for (int j = b; j < e; ++j) acc += A.csr_w[j] * (pc - A.pp[A.csr_col[j]]);
-      A.qq[c] = acc;
-      pq += pc * acc;
-    }
-    for (int c = wid; c < K; c += nwarp) {   // warp-uniform
-      const int b = A.row_ptr[c], e = A.row_ptr[c + 1];
-      if (e - b <= 32) continue;
-      const double pc = A.pp[c];
-      double acc = 0.0;
-#pragma unroll 4
-      for (int j = b + lane; j < e; j += 32) acc += A.csr_w[j] * (pc - A.pp[A.csr_col[j]]);
-      acc = warp_sum_d(acc);
-      if (lane == 0) {
-        A.qq[c] = acc;
-        pq += pc * acc;
+  // fixed-point grain: the number of terms of a sum is at most the launch's threads
+  const int S = 62 - (32 - __clz(gridDim.x * blockDim.x - 1));
+  // this CTA's rows and CSR slice
+  RowSlice RS;
+  {
+    const int per = (K + gridDim.x - 1) / gridDim.x;
+    RS.lo = min(K, blockIdx.x * per);
+    RS.hi = min(K, RS.lo + per);
+    RS.base = A.row_ptr[RS.lo];
+    const int nnz = A.row_ptr[RS.hi] - RS.base;
+    const long long need = 4ll * (RS.hi - RS.lo + 2) + 12ll * nnz + 16;
+    RS.cached = need <= (long long)A.smem_bytes;
+    if (RS.cached) {
+      int* rp = reinterpret_cast<int*>(dyn);
+      double* wv = reinterpret_cast<double*>(dyn + ((4 * (RS.hi - RS.lo + 2) + 15) & ~15));
+      int* cl = reinterpret_cast<int*>(wv + nnz);
+      for (int i = threadIdx.x; i <= RS.hi - RS.lo; i += blockDim.x) rp[i] = A.row_ptr[RS.lo + i] - RS.base;
+      for (int j = threadIdx.x; j < nnz; j += blockDim.x) {
+        wv[j] = A.csr_w[RS.base + j];
+        cl[j] = A.csr_col[RS.base + j];
       }
+      RS.rp = rp;
+      RS.col = cl;
+      RS.wgt = wv;
+      __syncthreads();
+    } else {
+      RS.rp = A.row_ptr;
+      RS.col = A.csr_col;
+      RS.wgt = A.csr_w;
     }
-    if (!grid_sum3(pq, d1, d2, A.red, ncall, st, sh)) return;
-    const double alpha = pq > 0.0 ? rz / pq : 0.0;
-    double rzn = 0, rrn = 0, d3 = 0;
-    for (int c = tid; c < K; c += nthr) {
-      A.s[c] += alpha * A.pp[c];
-      const double rc = A.r[c] - alpha * A.qq[c];
-      A.r[c] = rc;
-      const double zc = rc * A.diag[c];
-      A.z[c] = zc;
-      rzn += rc * zc;
-      rrn += rc * rc;
+  }
+  const double* __restrict__ invd = A.invd;
+  // x0 = 0: r0 = g, u0 = D^-1 g, w0 = L u0 (g and D are inputs: no sync needed)
+  double i0 = 0.0, i1 = 0.0, i2 = 0.0;   // gamma, delta, rho
+  spmv_rows(RS, [&](int j) { return invd[j] * A.g[j]; },
+            [&](int c, double uc, double wc) {
+              const double gc = A.g[c];
+              A.x[c] = 0.0;
+              A.p[c] = 0.0;
+              A.r[0][c] = gc;
+              A.q[0][c] = 0.0;
+              A.w[0][c] = wc;
+              return Terms3{gc * uc, wc * uc, gc * gc};
+            }, i0, i1, i2);
+  double ga = 0.0;
+  for (int c = RS.lo + threadIdx.x; c < RS.hi; c += blockDim.x) ga += A.gabs[c] * A.gabs[c];
+  // thread 0 keeps gamma, 1 / gamma and 1 / alpha of the previous iteration
+  double gamma = 0.0, rgamma = 0.0, ralpha = 0.0;
+  {
+    const double v4[4] = {i0, i1, i2, ga};   // gamma, delta, rho, sum gabs^2
+    Fx f4[4];
+    if (!reduce_fx<MODE, 4>(v4, f4, S, R, A.red, ncall, st)) return;
+    if (threadIdx.x == 0) {
+      const double gm = fx_double(f4[0], S), dl = fx_double(f4[1], S), rh = fx_double(f4[2], S);
+      // stop at the relative tolerance, or once the residual is at the rounding
+      // level of the terms that cancel in g (a system that is already solved has
+      // a right-hand side made of rounding noise)
+      const double floor2 = (64.0 * 1.1102230246251565e-16) * (64.0 * 1.1102230246251565e-16) * fx_double(f4[3], S);
+      const double stop2 = fmax(A.tol2 * rh, floor2);
+      const bool ok = dl > 0.0 && gm > 0.0;
+      sc[0] = ok ? gm / dl : 0.0;
+      sc[1] = 0.0;
+      sc[2] = (!(rh > 0.0) || rh <= stop2 || !ok) ? 1.0 : 0.0;
+      sc[3] = stop2;
+      gamma = gm;
+      rgamma = ok ? 1.0 / gm : 0.0;
+      ralpha = ok ? dl / gm : 0.0;
     }
-    if (!grid_sum3(rzn, rrn, d3, A.red, ncall, st, sh)) return;
-    const double beta = rz > 0.0 ? rzn / rz : 0.0;
-    rz = rzn;
+    __syncthreads();
+  }
+  double alpha = sc[0], beta = 0.0;
+  const double stop2 = sc[3];
+  bool done = sc[2] != 0.0;
+  int it = 0, b = 0;
+  while (!done && it < A.maxit) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;   // gamma', delta', rho'
+    if constexpr (MODE == 0) {
+      const double* __restrict__ ro = b ? A.r[1] : A.r[0];
+      const double* __restrict__ qo = b ? A.q[1] : A.q[0];
+      const double* __restrict__ wo = b ? A.w[1] : A.w[0];
+      double* __restrict__ rn = b ? A.r[0] : A.r[1];
+      double* __restrict__ qn = b ? A.q[0] : A.q[1];
+      double* __restrict__ wn = b ? A.w[0] : A.w[1];
+      spmv_rows(RS, [&](int j) { return invd[j] * fma(-alpha, fma(beta, qo[j], wo[j]), ro[j]); },
+                [&](int c, double uc, double wc) {
+                  const double qc = fma(beta, qo[c], wo[c]);
+                  const double rc = fma(-alpha, qc, ro[c]);
+                  const double pc = fma(beta, A.p[c], invd[c] * ro[c]);
+                  A.x[c] = fma(alpha, pc, A.x[c]);
+                  A.p[c] = pc;
+                  qn[c] = qc;
+                  rn[c] = rc;
+                  wn[c] = wc;
+                  return Terms3{rc * uc, wc * uc, rc * rc};
+                }, t0, t1, t2);
+      b ^= 1;
+    } else {
+      double* __restrict__ r = A.r[0];
+      double* __restrict__ q = A.q[0];
+      double* __restrict__ w = A.w[0];
+      double* __restrict__ u = A.u;
+      for (int c = RS.lo + threadIdx.x; c < RS.hi; c += blockDim.x) {
+        const double qc = fma(beta, q[c], w[c]);
+        const double rc = fma(-alpha, qc, r[c]);
+        const double pc = fma(beta, A.p[c], invd[c] * r[c]);
+        A.x[c] = fma(alpha, pc, A.x[c]);
+        A.p[c] = pc;
+        q[c] = qc;
+        r[c] = rc;
+        u[c] = invd[c] * rc;
+      }
+      cluster_barrier();
+      spmv_rows(RS, [&](int j) { return u[j]; },
+                [&](int c, double uc, double wc) {
+                  const double rc = r[c];
+                  w[c] = wc;
+                  return Terms3{rc * uc, wc * uc, rc * rc};
+                }, t0, t1, t2);
+    }
+    const double v3[3] = {t0, t1, t2};
+    Fx f3[3];
+    if (!reduce_fx<MODE, 3>(v3, f3, S, R, A.red, ncall, st)) return;
+    if (threadIdx.x == 0) {
+      const double gm = fx_double(f3[0], S), dl = fx_double(f3[1], S), rh = fx_double(f3[2], S);
+      const double bt = gm * rgamma;                  // gamma' / gamma
+      const double den = dl - bt * gm * ralpha;       // delta' - beta' gamma' / alpha
+      const bool ok = den > 0.0 && gm > 0.0;
+      const double rden = ok ? 1.0 / den : 0.0;       // the two divisions are independent
+      const double rgm = ok ? 1.0 / gm : 0.0;
+      sc[0] = gm * rden;
+      sc[1] = bt;
+      sc[2] = (rh <= stop2 || !ok) ? 1.0 : 0.0;
+      gamma = gm;
+      rgamma = rgm;
+      ralpha = den * rgm;                             // 1 / alpha'
+    }
+    __syncthreads();
+    alpha = sc[0];
+    beta = sc[1];
+    done = sc[2] != 0.0;   // sc is rewritten only after the next sum's CTA barriers
     ++it;
-    done = rrn <= stop2 || !(pq > 0.0);
-    if (!done) {
-      for (int c = tid; c < K; c += nthr) A.pp[c] = A.z[c] + beta * A.pp[c];
-      if (!gsync(st)) return;
-    }
   }
   // energy of the solved system: sum_p w_p D^2 + 2 h_p D + q_p, D = s_lo - s_hi
-  double en = 0, e1 = 0, e2 = 0;
-  for (int p = tid; p < P; p += nthr) {
-    const double D = A.s[A.p_lo[p]] - A.s[A.p_hi[p]];
-    en += A.p_acc[3 * p] * D * D + 2.0 * A.p_acc[3 * p + 1] * D + A.p_acc[3 * p + 2];
+  double en = 0.0;
+  {
+    const int per = (P + gridDim.x - 1) / gridDim.x;
+    const int p0 = min(P, (int)blockIdx.x * per), p1 = min(P, p0 + per);
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      const double D = A.x[A.p_lo[p]] - A.x[A.p_hi[p]];
+      en += A.p_acc[3 * p] * D * D + 2.0 * A.p_acc[3 * p + 1] * D + A.p_acc[3 * p + 2];
+    }
   }
-  if (!grid_sum3(en, e1, e2, A.red, ncall, st, sh)) return;
-  for (int c = tid; c < K; c += nthr) A.soff[c] += A.s[c];
-  if (tid == 0) {
+  const double v1[1] = {en};
+  Fx f1[1];
+  if (!reduce_fx<MODE, 1>(v1, f1, S, R, A.red, ncall, st)) return;
+  // no CTA of a cluster may exit while another still reads its shared memory
+  if constexpr (MODE == 1) cluster_barrier();
+  for (int c = RS.lo + threadIdx.x; c < RS.hi; c += blockDim.x) A.soff[c] += A.x[c];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double E = fx_double(f1[0], S);
     const int t = st->t + 1;
     st->t = t;
-    if (t <= NI_MAX_T) st->E[t] = en;
+    if (t <= NI_MAX_T) st->E[t] = E;
     st->scale_cg_last = it;
+    st->scale_cg_total += (unsigned long long)it;
     if (it > st->scale_cg_iters) st->scale_cg_iters = it;
     if (it >= A.maxit && !done) st->err |= NI_DEV_ERR_SCALE_NOCONV;
     bool conv = t >= A.T;
     if (!conv && t >= 4 && t <= NI_MAX_T) {
       const double e0 = st->E[t - 1];
-      conv = (e0 < 1e-300) || (fabs(en - e0) / e0 < A.dE_max);
+      conv = (e0 < 1e-300) || (fabs(E - e0) / e0 < A.dE_max);
     }
     st->converged = conv ? 1 : 0;
   }
 }
 
-// one CTA (no grid barrier) up to 8192 components; beyond, about 8 rows per warp
-// over several CTAs
+#define NI_SCALE_THREADS 256
+// dynamic shared memory of a scale PCG CTA: its slice of the quotient CSR
+#define NI_SCALE_SMEM (192 * 1024)
+
+static void scale_kernel_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute((const void*)k_scale_cg<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, NI_SCALE_SMEM);
+  cudaFuncSetAttribute((const void*)k_scale_cg<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, NI_SCALE_SMEM);
+  cudaFuncSetAttribute((const void*)k_scale_cg<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaGetLastError();
+  done = true;
+}
+// MODE 0: one CTA of 256 threads per 256 components, at most one per SM (the
+// FP64 rate is per SM), cooperatively launched when there is more than one
 int scale_cg_grid(ni_handle* h) {
-  if (h->Kcap <= 8192) return 1;
+  scale_kernel_attrs();
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scale_cg, 1024, 0);
-  int g = h->num_sms * std::max(1, std::min(per_sm, 2));
-  int need = (h->Kcap + 255) / 256;
-  return std::max(1, std::min(g, need));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scale_cg<0>, NI_SCALE_THREADS, NI_SCALE_SMEM);
+  if (per_sm < 1) return 1;
+  const int need = (h->Kcap + NI_SCALE_THREADS - 1) / NI_SCALE_THREADS;
+  return std::max(1, std::min(h->num_sms, need));
+}
+
+// Cluster-mode scale PCG: CTAs of 256 threads, 16 per cluster (a non-portable
+// size) where the device can schedule that, else 8, else none.
+#define NI_SCALE_CL_THREADS NI_SCALE_THREADS
+// auto mode (scale_solver = 0) takes the cluster up to this many components
+#define NI_SCALE_CL_AUTO_K 32768
+
+static cudaLaunchConfig_t cluster_cfg(int nc, cudaLaunchAttribute* at, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nc);
+  cfg.blockDim = dim3(NI_SCALE_CL_THREADS);
+  cfg.dynamicSmemBytes = NI_SCALE_SMEM;
+  cfg.stream = s;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = nc;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+int scale_cluster_size(ni_handle* h) {
+  if (h->scale_cluster >= 0) return h->scale_cluster;
+  h->scale_cluster = 0;
+  scale_kernel_attrs();
+  for (int nc = 16; nc >= 8; nc /= 2) {
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_cfg(nc, at, 0);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_scale_cg<1>, &cfg) == cudaSuccess && n >= 1) {
+      h->scale_cluster = nc;
+      break;
+    }
+    cudaGetLastError();
+  }
+  return h->scale_cluster;
+}
+
+static bool use_scale_cluster(ni_handle* h) {
+  if (h->cfg.scale_solver == 2) return false;
+  if (h->cfg.scale_solver == 0 && h->Kcap > NI_SCALE_CL_AUTO_K) return false;
+  return scale_cluster_size(h) > 0;
 }
 
 ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
@@ -793,26 +1170,41 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
                                                         h->sd, h->sv + 5 * (size_t)h->Kcap,
                                                         h->sv + 6 * (size_t)h->Kcap, h->csr_w); NI_COUNT(h);
   ScaleArgs sa;
+  const size_t kc = (size_t)h->Kcap;
   sa.st = st; sa.row_ptr = h->row_ptr; sa.csr_col = h->csr_col; sa.csr_w = h->csr_w; sa.csr_pair = h->csr_pair;
-  sa.p_lo = h->p_lo; sa.p_hi = h->p_hi; sa.p_acc = h->p_acc; sa.diag = h->sd;
-  sa.g = h->sv + 5 * (size_t)h->Kcap;
-  sa.gabs = h->sv + 6 * (size_t)h->Kcap;
-  sa.s = h->sv; sa.r = h->sv + (size_t)h->Kcap; sa.z = h->sv + 2 * (size_t)h->Kcap;
-  sa.pp = h->sv + 3 * (size_t)h->Kcap; sa.qq = h->sv + 4 * (size_t)h->Kcap;
-  sa.red = h->cacc;   // 12 doubles of scratch (component accumulators are free here)
+  sa.p_lo = h->p_lo; sa.p_hi = h->p_hi; sa.p_acc = h->p_acc; sa.invd = h->sd;
+  // h->sv: x, r0, r1, p, q0, g, gabs, q1, w0, w1, u (Kcap doubles each)
+  sa.g = h->sv + 5 * kc;
+  sa.gabs = h->sv + 6 * kc;
+  sa.x = h->sv;
+  sa.r[0] = h->sv + kc; sa.r[1] = h->sv + 2 * kc;
+  sa.p = h->sv + 3 * kc;
+  sa.q[0] = h->sv + 4 * kc; sa.q[1] = h->sv + 7 * kc;
+  sa.w[0] = h->sv + 8 * kc; sa.w[1] = h->sv + 9 * kc;
+  sa.u = h->sv + 10 * kc;
+  sa.red = reinterpret_cast<long long*>(h->cacc);   // 2 x grid x 8 (the component accumulators are free here)
+  sa.smem_bytes = NI_SCALE_SMEM;
   sa.soff = h->soff;
   sa.tol2 = h->cfg.scale_rtol * h->cfg.scale_rtol;
   sa.maxit = h->cfg.scale_maxit > 0 ? h->cfg.scale_maxit : std::min(4 * h->Kcap + 100, 200000);
   sa.T = h->cfg.T;
   sa.dE_max = h->cfg.dE_max;
+  if (use_scale_cluster(h)) {
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_cfg(h->scale_cluster, at, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_scale_cg<1>, sa);
+    NI_COUNT(h);
+    if (e != cudaSuccess) return ni_cuda_check(h, e, "scale PCG cluster launch");
+    return ni_cuda_check(h, cudaGetLastError(), "scale iteration");
+  }
   const int grid = scale_cg_grid(h);
   if (grid == 1) {
-    k_scale_cg<<<1, 1024, 0, s>>>(sa); NI_COUNT(h);
+    k_scale_cg<0><<<1, NI_SCALE_THREADS, NI_SCALE_SMEM, s>>>(sa); NI_COUNT(h);
   } else {
-    cudaMemsetAsync(h->cacc, 0, 12 * sizeof(double), s);
     cudaMemsetAsync(&st->bar, 0, sizeof(GridBar), s);
     void* args[] = {&sa};
-    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_scale_cg, dim3(grid), dim3(1024), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_scale_cg<0>, dim3(grid), dim3(NI_SCALE_THREADS), args,
+                                                NI_SCALE_SMEM, s);
     NI_COUNT(h);
     if (e != cudaSuccess) return ni_cuda_check(h, e, "scale PCG launch");
   }

@@ -41,7 +41,7 @@ class Config(C.Structure):
                 ("warm_start", C.c_int), ("hard_outliers", C.c_int), ("validate", C.c_int),
                 ("ctas_per_sm", C.c_int), ("mg_coarse_sweeps", C.c_int), ("precond", C.c_int), ("mg_omega", C.c_double),
                 ("mg_correction", C.c_double), ("mg_cta_cells", C.c_int), ("mg_flags", C.c_int),
-                ("fill_kernels", C.c_int)]
+                ("fill_kernels", C.c_int), ("scale_solver", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -52,7 +52,8 @@ class Stats(C.Structure):
                 ("fill_iters", C.c_int32), ("fill_unconverged", C.c_int32),
                 ("scale_cg_iters", C.c_int32), ("n_energy", C.c_int32), ("energy", C.c_double * 64),
                 ("ms_fill_solve", C.c_double), ("fill_px_iters", C.c_int64), ("kernel_launches", C.c_int64),
-                ("warm_fallbacks", C.c_int32), ("fill_fallbacks", C.c_int32)]
+                ("warm_fallbacks", C.c_int32), ("fill_fallbacks", C.c_int32),
+                ("scale_cg_total", C.c_int64)]
 
     def as_dict(self) -> Dict[str, object]:
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "energy"}
@@ -110,6 +111,11 @@ class NIError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+
+
+def default_net_path() -> str:
+    """The trained warm-start network shipped with the package."""
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "nets", "warmstart_256.bin")
 
 
 def default_config(H: int, W: int) -> Config:
