@@ -1,12 +1,12 @@
 // Learned warm start (not in the paper; an extension beyond it): a 6-layer
 // 3x3 convolutional network trained and run with BF16 tensor-core kernels.
 //
-// Convolutions are implicit GEMMs on mma.sync.m16n8k16 (BF16 inputs, FP32
-// accumulation).  A warp owns 16 consecutive output pixels of one row and all
-// output channels; the K dimension runs over the 9 taps and the input channels
-// (channels are contiguous in NHWC, so a fragment register is one 32-bit load).
+// The forward and dgrad convolutions are implicit GEMMs on the tcgen05 tensor
+// cores with the accumulator in tensor memory (ni_cnn_tc.cu):
 //   forward  out = relu(conv_valid(in, W) + b)            (layers 1-5), linear (6)
 //   dgrad    g_{l-1} = conv_valid(pad2(g_l), flip(W)^T) * [act_{l-1} > 0]
+// The weight gradient, a GEMM whose reduction runs over the pixels, stays on
+// mma.sync.m16n8k16 (BF16 inputs, FP32 accumulation):
 //   wgrad    dW[tap] (cout x cin) = sum_px g[px] act[px + tap]^T  (K = pixels)
 // Channel counts are padded for the 16-wide K steps: the 4 input channels to 16,
 // the 5 output channels to 8 (forward) and 16 (gradient of the last layer).
@@ -21,6 +21,11 @@
 #include "ni_internal.cuh"
 
 typedef __nv_bfloat16 bf16;
+
+// ni_cnn_tc.cu
+cudaError_t conv3x3_tc(const bf16* in, int B, int Hi, int ci, int co, int wco, int mode, const bf16* w,
+                       const float* bias, int nbias, void* out, const bf16* act_mask, int* err, int num_sms,
+                       cudaStream_t s);
 
 namespace {
 
@@ -57,79 +62,6 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// ---------------------------------------------------------------------------
-// valid 3x3 convolution, NHWC bf16 in, weights [9][COUTP][CIN_P]
-//   MODE 0: out bf16 = relu(acc + b)
-//   MODE 1: out float = acc + b                      (last layer)
-//   MODE 2: out bf16 = acc * [act_mask > 0]          (dgrad with the ReLU mask)
-// ---------------------------------------------------------------------------
-template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(128) k_conv(const bf16* __restrict__ in, int B, int Hi, int Wi,
-                                               const bf16* __restrict__ w, const float* __restrict__ bias,
-                                               void* __restrict__ out, const bf16* __restrict__ act_mask) {
-  static_assert(CI % 16 == 0 && CO % 8 == 0, "padded channel counts");
-  constexpr int NT = CO / 8;
-  const int Ho = Hi - 2, Wo = Wi - 2;
-  const int nseg = (Wo + 15) / 16;
-  const long long items = (long long)B * Ho * nseg;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
-  for (long long it = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < items; it += wstride) {
-    const int seg = (int)(it % nseg);
-    const long long ny = it / nseg;
-    const int y = (int)(ny % Ho), n = (int)(ny / Ho);
-    const int x0 = seg * 16;
-    const bool v0 = x0 + g < Wo, v1 = x0 + g + 8 < Wo;
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int dy = tap / 3, dx = tap % 3;
-      const bf16* row = in + (((long long)n * Hi + y + dy) * Wi + x0 + dx) * CI;
-#pragma unroll
-      for (int s = 0; s < CI / 16; ++s) {
-        const int c0 = s * 16 + 2 * t;
-        const uint32_t a0 = v0 ? ld32(row + (long long)g * CI + c0) : 0u;
-        const uint32_t a1 = v1 ? ld32(row + (long long)(g + 8) * CI + c0) : 0u;
-        const uint32_t a2 = v0 ? ld32(row + (long long)g * CI + c0 + 8) : 0u;
-        const uint32_t a3 = v1 ? ld32(row + (long long)(g + 8) * CI + c0 + 8) : 0u;
-#pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          const bf16* wp = w + ((long long)tap * CO + j * 8 + g) * CI + c0;
-          mma_bf16(acc[j], a0, a1, a2, a3, ld32(wp), ld32(wp + 8));
-        }
-      }
-    }
-    // epilogue: rows g and g + 8 are pixels x0 + g, x0 + g + 8; columns 2t, 2t + 1
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int xr = x0 + g + 8 * half;
-      if (xr >= Wo) continue;
-      const long long o = (((long long)n * Ho + y) * Wo + xr) * CO;
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const int co = j * 8 + 2 * t;
-        float u0 = acc[j][2 * half], u1 = acc[j][2 * half + 1];
-        if (MODE != 2 && bias) { u0 += bias[co]; u1 += bias[co + 1]; }
-        if (MODE == 0) {
-          *reinterpret_cast<uint32_t*>(static_cast<bf16*>(out) + o + co) = pack_bf16(fmaxf(u0, 0.f), fmaxf(u1, 0.f));
-        } else if (MODE == 1) {
-          float* of = static_cast<float*>(out) + o + co;
-          of[0] = u0;
-          of[1] = u1;
-        } else {
-          const bf16* am = act_mask + o + co;
-          const float m0 = __bfloat162float(am[0]) > 0.f ? 1.f : 0.f;
-          const float m1 = __bfloat162float(am[1]) > 0.f ? 1.f : 0.f;
-          *reinterpret_cast<uint32_t*>(static_cast<bf16*>(out) + o + co) = pack_bf16(u0 * m0, u1 * m1);
-        }
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // weight gradient: dW[tap][co][ci] += sum over output pixels of g[px][co] * act[px + tap][ci]
@@ -440,6 +372,8 @@ struct ni_cnn {
   bf16* pad = nullptr;  // padded gradient
   unsigned long long* cnt = nullptr;
   double* loss = nullptr;
+  int* err = nullptr;   // NI_DEV_ERR_* bits of the tensor-core kernels
+  int num_sms = 1;
   long long step = 0;
 };
 
@@ -490,6 +424,13 @@ extern "C" ni_status ni_cnn_create(int max_batch, int tile, uint64_t seed, ni_cn
   if (e == cudaSuccess) e = alloc(&net->pad, (size_t)max_batch * (S + 4) * (S + 4) * 32);
   if (e == cudaSuccess) e = alloc(&net->cnt, 2);
   if (e == cudaSuccess) e = alloc(&net->loss, 2);
+  if (e == cudaSuccess) e = alloc(&net->err, 1);
+  if (e == cudaSuccess) e = cudaMemset(net->err, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   if (e != cudaSuccess) {
     ni_cnn_destroy(net);
     return e == cudaErrorMemoryAllocation ? NI_ERR_OOM : NI_ERR_CUDA;
@@ -521,7 +462,7 @@ extern "C" ni_status ni_cnn_destroy(ni_cnn* net) {
   cudaFree(net->p); cudaFree(net->g); cudaFree(net->m); cudaFree(net->v);
   for (int l = 0; l < NL; ++l) { cudaFree(net->wf[l]); cudaFree(net->wdg[l]); cudaFree(net->act[l]); }
   cudaFree(net->out); cudaFree(net->gbuf[0]); cudaFree(net->gbuf[1]); cudaFree(net->pad);
-  cudaFree(net->cnt); cudaFree(net->loss);
+  cudaFree(net->cnt); cudaFree(net->loss); cudaFree(net->err);
   delete net;
   return NI_OK;
 }
@@ -545,18 +486,15 @@ extern "C" ni_status ni_cnn_set_params(ni_cnn* net, const float* host) {
 static void forward(ni_cnn* net, const float* in, int B, cudaStream_t s) {
   const long long npx0 = (long long)B * net->S * net->S;
   k_pack_input<<<grid_of(npx0, 256), 256, 0, s>>>(in, npx0, net->act[0]);
-  const int cap = 4096;
   for (int l = 0; l < NL; ++l) {
     const int Hi = side(net, l);
-    const long long items = (long long)B * (Hi - 2) * ((Hi - 2 + 15) / 16);
-    const int grid = grid_of(items, 4, cap);
     const float* bias = net->p + param_offset(l) + w_size(l);
-    if (l == 0)
-      k_conv<16, 32, 0><<<grid, 128, 0, s>>>(net->act[0], B, Hi, Hi, net->wf[0], bias, net->act[1], nullptr);
-    else if (l < NL - 1)
-      k_conv<32, 32, 0><<<grid, 128, 0, s>>>(net->act[l], B, Hi, Hi, net->wf[l], bias, net->act[l + 1], nullptr);
-    else
-      k_conv<32, 8, 1><<<grid, 128, 0, s>>>(net->act[l], B, Hi, Hi, net->wf[l], bias, net->out, nullptr);
+    if (l < NL - 1)
+      conv3x3_tc(net->act[l], B, Hi, CINP[l], 32, 32, 0, net->wf[l], bias, COUT[l], net->act[l + 1], nullptr,
+                 net->err, net->num_sms, s);
+    else   // the 8 stored output channels padded to 16 for the MMA's N
+      conv3x3_tc(net->act[l], B, Hi, 32, 16, 8, 1, net->wf[l], bias, COUT[l], net->out, nullptr, net->err,
+                 net->num_sms, s);
   }
 }
 
@@ -605,11 +543,7 @@ static ni_status backward(ni_cnn* net, const float* in, const float* tz, const i
     const int Hp = Ho + 4;
     k_pad2<<<grid_of((long long)B * Hp * Hp * gc / 2, 256), 256, 0, s>>>(gcur, B, Ho, Ho, gc, net->pad);
     bf16* gnext = (gcur == net->gbuf[0]) ? net->gbuf[1] : net->gbuf[0];
-    const long long it2 = (long long)B * (Ho + 2) * ((Ho + 2 + 15) / 16);
-    if (l == NL - 1)
-      k_conv<16, 32, 2><<<grid_of(it2, 4), 128, 0, s>>>(net->pad, B, Hp, Hp, net->wdg[l], nullptr, gnext, net->act[l]);
-    else
-      k_conv<32, 32, 2><<<grid_of(it2, 4), 128, 0, s>>>(net->pad, B, Hp, Hp, net->wdg[l], nullptr, gnext, net->act[l]);
+    conv3x3_tc(net->pad, B, Hp, gc, 32, 32, 2, net->wdg[l], nullptr, 0, gnext, net->act[l], net->err, net->num_sms, s);
     gcur = gnext;
   }
   double lh[2];
