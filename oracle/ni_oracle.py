@@ -611,15 +611,63 @@ def quotient_components(K, labels, geo: Geometry, e):
     return cc, ncc
 
 
+SCALE_RTOL = 1e-12
+SCALE_FLOOR = 64.0 * 2.0 ** -53
+
+
 def solve_scales(A, rhs, w, K, qcc, nq):
-    """s~ <- cg(A^T W A, A^T W b) (Eq. 14) from s~ = 0.  The oracle computes the
-    result CG converges to, the minimum-norm least-squares solution (zero mean
-    over the nodes of each connected component of Q_m), directly."""
+    """s~ <- cg(A^T W A, A^T W b) (Eq. 14) from s~ = 0, as the paper states it.
+
+    Reading: the weights of t >= 2 (BiNI times W^out, Eqs. 5 and 11) span
+    hundreds of decades on large maps, so this Laplacian can be singular to
+    working precision away from its exact null space; a direct solve then
+    turns the rounding noise of the right-hand side into arbitrarily large
+    offsets, while CG, the solver the paper names, leaves those directions
+    nearly untouched.  So the oracle runs CG: Jacobi-preconditioned, FP64, from
+    0, until ||g - M s|| <= 1e-12 ||g|| or the residual reaches the rounding
+    level of g, 64 eps ||g_abs||, where g_abs sums the absolute values of the
+    terms that make up g (a system that is already solved has a right-hand
+    side made of rounding noise); at most 4 K + 100 iterations.  The result is
+    then given the minimum-norm gauge: zero mean on every block of M's weighted
+    graph and on every connected component of Q_m.  Where M is well
+    conditioned this is the minimum-norm least-squares solution (pinned against
+    the dense pseudo-inverse in tests/test_oracle_pins.py).
+    Returns (s~, CG iterations)."""
     Wd = sp.diags(w)
     M = (A.T @ Wd @ A).tocsr()
-    g = A.T @ (w * rhs)
-    s = solve_min_norm(M, g)
-    return project_zero_mean(s, qcc, nq), 1
+    wb = w * rhs
+    g = A.T @ wb
+    gabs = abs(A).T @ np.abs(wb)
+    n = M.shape[0]
+    d = M.diagonal()
+    inv = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    stop2 = max(SCALE_RTOL ** 2 * float(g @ g), SCALE_FLOOR ** 2 * float(gabs @ gabs))
+    x = np.zeros(n)
+    r = np.asarray(g, np.float64).copy()
+    it = 0
+    if float(r @ r) > stop2:
+        z = inv * r
+        p = z.copy()
+        rz = float(r @ z)
+        for it in range(1, 4 * n + 101):
+            q = M @ p
+            pq = float(p @ q)
+            if not pq > 0.0:
+                break
+            alpha = rz / pq
+            x += alpha * p
+            r -= alpha * q
+            if float(r @ r) <= stop2:
+                break
+            z = inv * r
+            rz_new = float(r @ z)
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+    off = M - sp.diags(d)
+    off.eliminate_zeros()
+    nb, blk = connected_components(off, directed=False)
+    x = project_zero_mean(x, blk, nb)
+    return project_zero_mean(x, qcc, nq), it
 
 
 def energy(A, rhs, w, s):
