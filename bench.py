@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Throughput of continuous-component normal integration on one GB300.
 
-One step = one pass of the whole hot path (seeding, fill, relative-scale loop
-with merging, output) over one synthetic normal map through ni_integrate.
-Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
-(the reference arm) on a bounded sample of the same workload.
+One step = one pass of the whole hot path (seeding, learned warm start, fill,
+relative-scale loop with merging, output) over one synthetic normal map
+through ni_integrate.  The default workload is the 8192 x 8192 map (4.4e7
+valid pixels, 600 cells) with the full pipeline: seeding, the batched
+multigrid-preconditioned fill from the network's warm start, the
+relative-scale loop with three merge rounds.  Prints ONE JSON line (rank 0).
+`--impl reference` times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.
 
 Multi-GPU: replicas only (each rank integrates its own copy of the map; one
 map's path has no exchange step here), value = all ranks' valid pixels /
@@ -27,9 +31,12 @@ sys.path.insert(0, ROOT)
 METRIC = ("valid Mpixel/s integrated at ≤1e-3 rel depth RMSE vs FP64 oracle; "
           "stencil GB/s vs HBM peak")
 UNIT = "Mpixel/s"
-# Algorithmic bytes per active pixel and iteration of the fill kernels.
-# Jacobi (k_pcg_tiles): read p, x, r (4 B each), the right/down weights (8 B),
-# the inverse diagonal (4 B) and the label (4 B); write p, x, r (4 B each).
+# Algorithmic bytes per active pixel and iteration of a fill PCG iteration, the
+# least a Jacobi PCG must move: read the right/down weights (8 B), the inverse
+# diagonal (4 B), p (4 B), x and r (8 B); write x and r (8 B) and p (4 B).
+ALG_BYTES_PER_PX_ITER = 36
+# Jacobi (k_pcg_tiles) as built: read p, x, r (4 B each), the right/down weights
+# (8 B), the inverse diagonal (4 B) and the label (4 B); write p, x, r (4 B each).
 PCG_BYTES_PER_PX_ITER = 40
 # Multigrid (k_pcg_mg), level 0 in four passes: restriction reads r, 1/d,
 # w right/down (16 B) and the aggregation flag (1 B) and writes a quarter of a
@@ -48,7 +55,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3")
+    ap.add_argument("--config", default="c5")
+    ap.add_argument("--warm-start", default="auto", choices=["auto", "0", "1"],
+                    help="learned warm start of the fill (auto: on for the 8192^2 and 4096^2 maps)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the plain-PCG and cold-start lines reported beside the headline")
     ap.add_argument("--variant", default="batched", choices=["batched", "plain"])
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--precond", type=int, default=1, help="batched fill: 0 Jacobi, 1 multigrid")
@@ -160,6 +171,107 @@ def replica_throughput(seconds: float, units_per_rank: int, steps: int) -> float
     return units_per_rank * steps * world / seconds / 1e6
 
 
+def oracle_workers():
+    return max(1, os.cpu_count() or 1)
+
+
+# bounded samples of each workload for the oracle timings: top-left crops
+CROP = {"c5": 1024, "c4_eval": 1024, "c3": 1024}
+# the reference arm's per-step sample (each of its warm-up and timed steps runs it)
+REF_CROP = {"c5": 512, "c4_eval": 512, "c3": 512}
+
+
+def crop_of(w, size):
+    import numpy as np
+    H, W = w.mask.shape
+    h, wd = min(H, size), min(W, size)
+    return np.ascontiguousarray(w.normals[:h, :wd]), np.ascontiguousarray(w.mask[:h, :wd])
+
+
+def time_oracle_crop(w, params, size, workers):
+    """The oracle (as it stands) on the top-left size x size crop of the map:
+    (seconds, valid pixels, sample description)."""
+    import oracle as O
+    nrm, msk = crop_of(w, size)
+    t0 = time.perf_counter()
+    O.integrate(nrm, msk, w.camera, O.Params.from_dict(params), workers=workers)
+    dt = time.perf_counter() - t0
+    nv = int(msk.sum())
+    return dt, nv, f"top-left {msk.shape[0]}x{msk.shape[1]} crop of {w.name} ({nv} valid px), {workers} processes"
+
+
+def partition_mismatch(a, b):
+    """Where two partitions, given as maps seeding component -> group label (a
+    and b), differ: (seeding components in a group of either partition that is
+    not also exactly a group of the other, such groups of a, such groups of b)."""
+    import numpy as np
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    pair = a * (int(b.max()) + 1 if b.size else 1) + b
+    _, inv_p = np.unique(pair, return_inverse=True)
+    _, inv_a = np.unique(a, return_inverse=True)
+    _, inv_b = np.unique(b, return_inverse=True)
+    # a group matches if its seeding components form one (a, b) pair class and
+    # that class is the whole group on both sides
+    n_pa = np.bincount(inv_p)[inv_p]
+    n_a = np.bincount(inv_a)[inv_a]
+    n_b = np.bincount(inv_b)[inv_b]
+    bad = (n_pa != n_a) | (n_pa != n_b)
+    return int(np.sum(bad)), int(np.unique(a[bad]).size), int(np.unique(b[bad]).size)
+
+
+def digest_check(w, depth, labels, labels0, st):
+    """Compare a GPU run with the stored FP64 oracle digest of the same
+    workload (tests/golden/<workload>.oracle.npz, written by
+    tests/golden/make_oracle_digest.py from oracle/ only): seeding labels
+    bit for bit, the partition after every merge as a map seeding label ->
+    label, and the depth at the digest's sampled pixels after the
+    per-island scale alignment.  None if there is no digest."""
+    import hashlib
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"{w.name}.oracle.npz")
+    if not os.path.exists(path):
+        return None
+    D = np.load(path)
+    meta = json.loads(str(D["meta"]))
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(w.normals, dtype=np.float32).tobytes())
+    h.update(np.ascontiguousarray(w.mask, dtype=np.uint8).tobytes())
+    same_input = h.hexdigest() == str(D["input_sha256"])
+    l0 = np.ascontiguousarray(labels0, dtype=np.int32)
+    lf = np.ascontiguousarray(labels, dtype=np.int32)
+    lab0_ok = hashlib.sha256(l0.tobytes()).hexdigest() == str(D["labels0_sha256"])
+    lab_ok = hashlib.sha256(lf.tobytes()).hexdigest() == str(D["labels_sha256"])
+    # final partition as a map seeding label -> final label (seeding labels bit-exact)
+    K0 = int(D["K0"])
+    flat0, flatf = l0.reshape(-1), lf.reshape(-1)
+    first = np.full(K0, flat0.size, np.int64)
+    v = flat0 >= 0
+    np.minimum.at(first, flat0[v], np.nonzero(v)[0])
+    part_diff = None
+    if lab0_ok and len(D["merge_maps"]):
+        nc, ga, gb = partition_mismatch(flatf[first], D["merge_maps"][-1])
+        part_diff = {"seed_components": nc, "gpu_groups": ga, "oracle_groups": gb}
+    # sampled depth, aligned per island by the best scale on the samples
+    idx, isl, ref = D["sample_idx"].astype(np.int64), D["sample_island"], D["sample_depth"]
+    z = np.asarray(depth, np.float64).reshape(-1)[idx]
+    al = np.empty_like(z)
+    for i in np.unique(isl):
+        s = isl == i
+        den = float(np.sum(z[s] * z[s]))
+        al[s] = z[s] * (float(np.sum(z[s] * ref[s])) / den if den > 0 else 1.0)
+    rmse = float(np.sqrt(np.mean((al - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)))
+    mx = float(np.max(np.abs(al - ref) / np.abs(ref)))
+    return {"oracle": "stored FP64 digest of the full map (tests/golden)", "input_matches_digest": same_input,
+            "labels0_bit_exact": lab0_ok, "K0": st["K0"], "oracle_K0": K0,
+            "labels_bit_exact": lab_ok, "K_final": st["K_final"], "oracle_K_final": int(D["K"]),
+            "final_groups_not_matched": part_diff,
+            "iters": st["scale_iters"], "oracle_iters": int(D["iters"]),
+            "rel_rmse_vs_oracle": rmse, "max_rel_err_vs_oracle": mx, "samples": int(idx.size),
+            "tolerance": 1e-4, "oracle_seconds": meta.get("oracle_seconds"),
+            "oracle_host": f"{meta.get('host')}, {meta.get('workers')} processes"}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -195,10 +307,6 @@ def run_ours(args):
     import torch.distributed as dist
 
     rank, world, local = dist_env()
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2510_11508_gb300 import ni
     from synth import make_workload
 
     w = make_workload(args.config)
@@ -206,29 +314,59 @@ def run_ours(args):
     params = dict(w.params)
     if args.pixel_level:
         params["theta_c_deg"] = None
-    cfg = ni.config_for(H, W, w.camera, params, batched=1 if args.variant == "batched" else 0,
-                        precision=args.precision, precond=args.precond)
-    it = ni.Integrator(cfg)
-    n = torch.from_numpy(w.normals).cuda()
-    m = torch.from_numpy(w.mask).cuda()
+    warm = (args.config in ("c5", "c4_eval")) if args.warm_start == "auto" else args.warm_start == "1"
     n_valid = int(w.mask.sum())
 
-    # accuracy against the FP64 oracle (rank 0), which is also the CPU baseline
-    check = None
+    # CPU baseline: the oracle on a bounded crop of the same map, all host cores
+    # (its process pool is spawned before the first CUDA call)
     cpu = None
+    live_oracle = not os.path.exists(os.path.join(ROOT, "tests", "golden", f"{w.name}.oracle.npz"))
+    if rank == 0 and not args.no_check and not live_oracle:
+        nw = oracle_workers()
+        dt, nv, sample = time_oracle_crop(w, params, CROP.get(args.config, 1024), nw)
+        cpu = {"value": nv / dt / 1e6, "unit": UNIT, "cores": nw, "kind": "oracle", "sample": f"{sample}, {dt:.1f} s"}
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2510_11508_gb300 import ni
+
+    def make(**over):
+        kw = dict(batched=1 if args.variant == "batched" else 0, precision=args.precision, precond=args.precond)
+        kw.update(over)
+        cfg = ni.config_for(H, W, w.camera, params, **kw)
+        it = ni.Integrator(cfg)
+        if cfg.warm_start:
+            it.load_net(ni.default_net_path())
+        return it
+
+    it = make(warm_start=1 if warm else 0)
+    n = torch.from_numpy(w.normals).cuda()
+    m = torch.from_numpy(w.mask).cuda()
+
+    # accuracy against the FP64 oracle (rank 0)
+    check = None
+    labels0, K0 = it.seed_components(n, m)
     depth, labels, st = it.integrate(n, m)
     torch.cuda.synchronize()
     if rank == 0 and not args.no_check:
-        import oracle as O
-        t0 = time.perf_counter()
-        ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(params))
-        dt = time.perf_counter() - t0
-        d = depth.cpu().numpy()
-        err = O.aligned_rel_rmse(np.where(w.mask > 0, d, np.nan), ref["depth"], w.mask, w.camera["camera"])
-        lab_ok = bool(np.array_equal(labels.cpu().numpy(), ref["labels"]))
-        check = {"rel_rmse_vs_oracle": err, "labels_bit_exact": lab_ok, "K0": st["K0"],
-                 "K_final": st["K_final"], "oracle_K_final": ref["K"], "iters": st["scale_iters"],
-                 "oracle_iters": ref["iters"], "tolerance": 1e-4 if args.precision == 0 else 1e-3}
+        if not live_oracle:
+            check = digest_check(w, depth.cpu().numpy(), labels.cpu().numpy(), labels0.cpu().numpy(), st)
+        else:
+            import oracle as O
+            nw = oracle_workers()
+            t0 = time.perf_counter()
+            ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(params), workers=nw)
+            dt = time.perf_counter() - t0
+            d = depth.cpu().numpy()
+            err = O.aligned_rel_rmse(np.where(w.mask > 0, d, np.nan), ref["depth"], w.mask, w.camera["camera"])
+            lab_ok = bool(np.array_equal(labels.cpu().numpy(), ref["labels"]))
+            check = {"oracle": "FP64 oracle run on the full map", "rel_rmse_vs_oracle": err,
+                     "labels_bit_exact": lab_ok, "K0": st["K0"], "oracle_K0": ref["K0"],
+                     "K_final": st["K_final"], "oracle_K_final": ref["K"], "iters": st["scale_iters"],
+                     "oracle_iters": ref["iters"], "tolerance": 1e-4 if args.precision == 0 else 1e-3}
+            cpu = {"value": n_valid / dt / 1e6, "unit": UNIT, "cores": nw, "kind": "oracle",
+                   "sample": f"the full {w.name} workload ({n_valid} valid px), one run, {nw} processes, {dt:.1f} s"}
         # error against the synthetic ground truth: MADE after the best scale (offset) of each island
         gt32 = np.ascontiguousarray(w.depth_gt, dtype=np.float32)
         isl, n_isl = mask_islands(w.mask)
@@ -238,9 +376,6 @@ def run_ours(args):
         except (ni.NIError, ValueError) as e:   # a diagnostic: report, do not stop the bench
             check["made_vs_gt"] = None
             check["made_error"] = str(e)
-        check["oracle_made_vs_gt"] = O.min_made(ref["depth"], gt32, isl, n_isl, w.camera["camera"])[0]
-        cpu = {"value": n_valid / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the full {w.name} workload ({n_valid} valid px), one run, {dt:.1f} s"}
 
     for _ in range(args.warmup):
         it.integrate(n, m)
@@ -261,6 +396,7 @@ def run_ours(args):
         time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fill_ms, px_iters, launches = 0.0, 0, 0
+    stage_sum = {}
     e0.record(stream)
     for _ in range(args.steps):
         flush.zero_()
@@ -268,6 +404,8 @@ def run_ours(args):
         fill_ms += st["ms_fill_solve"]
         px_iters += st["fill_px_iters"]
         launches += st["kernel_launches"] + 1
+        for k in ("ms_seed", "ms_fill", "ms_scale", "ms_output", "ms_total"):
+            stage_sum[k] = stage_sum.get(k, 0.0) + st[k]
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
@@ -293,6 +431,50 @@ def run_ours(args):
            "h2d_bytes_per_step": int(nh.numel() * 4 + mh.numel()),
            "d2h_bytes_per_step": int(out.numel() * 4)}
 
+    # the other paths on the same map, same box (outside the timed region)
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = {}
+        others = [("batched_cold_start", dict(warm_start=0), 3),
+                  ("batched_jacobi_cold_start", dict(warm_start=0, precond=0), 1),
+                  ("plain_global_jacobi_pcg", dict(warm_start=0, batched=0), 1)]
+        if not warm:
+            others = others[1:]
+        for name, over, reps in others:
+            if name.startswith("plain") and H * W > (1 << 22):
+                # one global CG over every component: on the 4096^2 and 8192^2
+                # maps it does not reach the tolerance within cg_maxit = 20000
+                variants[name] = {"skipped": "the single global Jacobi PCG needs more than cg_maxit iterations "
+                                             "on maps beyond 2048 x 2048"}
+                continue
+            iv = make(**over)
+            try:
+                iv.integrate(n, m)
+            except ni.NIError as e:
+                variants[name] = {"error": str(e)}
+                iv.close()
+                continue
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                dv, lv, sv = iv.integrate(n, m)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a0.elapsed_time(a1))
+            tm = statistics.median(ts)
+            d0 = depth.cpu().numpy()
+            d1 = dv.cpu().numpy()
+            ok = np.isfinite(d0) & np.isfinite(d1)
+            variants[name] = {"ms_per_map": tm, "value": n_valid / tm / 1e3, "unit": UNIT,
+                              "fill_iters": sv["fill_iters"], "scale_iters": sv["scale_iters"],
+                              "K_final": sv["K_final"], "ms_fill": sv["ms_fill"], "ms_scale": sv["ms_scale"],
+                              "labels_equal_headline": bool(np.array_equal(lv.cpu().numpy(), labels.cpu().numpy())),
+                              "max_rel_diff_vs_headline": float(np.max(np.abs(d1[ok] / d0[ok] - 1.0)))}
+            iv.close()
+
     peak, peak_src = peaks()
     per_launch_ms = fill_ms / args.steps
     if args.variant == "batched" and args.precond == 1:
@@ -301,16 +483,19 @@ def run_ours(args):
         kernel, source, bpp = "k_pcg_tiles", "ni_fill.cu", PCG_BYTES_PER_PX_ITER
     else:
         kernel, source, bpp = "k_cg_spmv+k_cg_update+k_cg_dir", "ni_fill.cu", PCG_BYTES_PER_PX_ITER
-    per_launch_bytes = bpp * px_iters / args.steps
-    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
+    units = px_iters / args.steps
+    alg_bytes = ALG_BYTES_PER_PX_ITER * units
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
+    built = bpp * units / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     tpi = traffic_per_px_iter(kernel, source)
     roof = {"kernel": kernel,
             "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
-            "traffic": (tpi * px_iters / args.steps) if tpi is not None else None,
-            "algorithmic_bytes_per_launch": per_launch_bytes,
-            "bytes_per_px_iter": bpp,
-            "px_iters_per_launch": px_iters / args.steps, "ms_per_launch": per_launch_ms}
+            "traffic": (tpi * units) if tpi is not None else None,
+            "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_px_iter": ALG_BYTES_PER_PX_ITER,
+            "px_iters_per_launch": units, "ms_per_launch": per_launch_ms,
+            "kernel_bytes_per_px_iter": bpp, "kernel_achieved": built,
+            "kernel_frac": (built / peak) if built else None}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -318,16 +503,18 @@ def run_ours(args):
                        "n_valid": n_valid, "variant": args.variant,
                        "fill_preconditioner": ("multigrid V-cycle" if args.precond == 1 else "Jacobi")
                        if args.variant == "batched" else "Jacobi",
+                       "warm_start": "learned (6-layer BF16 conv net)" if warm else "none",
                        "reductions": "fp64" if args.precision == 0 else "fp32 tree + fp64 across CTAs",
-                       "theta_c_deg": params["theta_c_deg"], "T": params["T"],
+                       "theta_c_deg": params["theta_c_deg"], "T": params["T"], "dE_max": params["dE_max"],
                        "can_merge": params["can_merge"], "freq_merging": params["freq_merging"],
                        "l2": "flushed between steps (256 MiB write inside the timed region)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks, "check": check,
-            "stages_ms": {k: st[k] for k in ("ms_seed", "ms_fill", "ms_scale", "ms_output", "ms_total")},
-            "fill_iters": st["fill_iters"], "scale_iters": st["scale_iters"],
-            "K0": st["K0"], "K_final": st["K_final"]}
+            "stages_ms": {k: v / args.steps for k, v in stage_sum.items()},
+            "fill_iters": st["fill_iters"], "scale_iters": st["scale_iters"], "merges": st["merges"],
+            "scale_cg_iters_total": st["scale_cg_total"], "warm_fallbacks": st["warm_fallbacks"],
+            "K0": st["K0"], "K_final": st["K_final"], "variants": variants}
     if rank == 0:
         print(json.dumps(line), flush=True)
     it.close()
@@ -339,8 +526,6 @@ def run_ours(args):
 # reference arm: the FP64 CPU oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 def run_reference(args):
-    import numpy as np
-
     rank, world, local = dist_env()
     if rank != 0:
         return
@@ -348,25 +533,26 @@ def run_reference(args):
     from synth import make_workload
 
     w = make_workload(args.config)
-    crop = 512
-    nrm = np.ascontiguousarray(w.normals[:crop, :crop])
-    msk = np.ascontiguousarray(w.mask[:crop, :crop])
+    nw = oracle_workers()
+    size = REF_CROP.get(args.config, 512)
+    nrm, msk = crop_of(w, size)
     n_valid = int(msk.sum())
     p = O.Params.from_dict(w.params)
     for _ in range(args.warmup):
-        O.integrate(nrm, msk, w.camera, p)
+        O.integrate(nrm, msk, w.camera, p, workers=nw)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.integrate(nrm, msk, w.camera, p)
+        O.integrate(nrm, msk, w.camera, p, workers=nw)
     dt = time.perf_counter() - t0
     value = n_valid * args.steps / dt / 1e6
-    sample = f"top-left {crop}x{crop} crop of {w.name} ({n_valid} valid px) per step"
+    sample = (f"top-left {msk.shape[0]}x{msk.shape[1]} crop of {w.name} ({n_valid} valid px) per step, "
+              f"{nw} processes")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": w.name, "sample": sample, "variant": "fp64 CPU oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nw, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

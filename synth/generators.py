@@ -453,7 +453,9 @@ def c5_map(H=8192, W=8192, n_cells=600, valid_frac=0.67, seed=1005, noise=0.01,
     m8 = mask.astype(np.uint8)
     return Workload(name, nrm, m8, Z, cam,
                     params if params is not None else
-                    _params(theta_c_deg=3.5, can_merge=True, freq_merging=5),
+                    # T = 15 with a merge every 5 iterations and no early stop:
+                    # three merge rounds
+                    _params(theta_c_deg=3.5, can_merge=True, freq_merging=5, dE_max=0.0),
                     f"{H}x{W} perspective, {n_cells} cells (sphere caps, tori, bump patches), "
                     f"noise {noise}", cells)
 

@@ -14,6 +14,10 @@ this script stores what a GPU run is checked against without re-running it:
   sample_idx        seeded sample of valid pixels (raster indices, sorted)
   sample_island     island of the mask (4-connected valid region) of each
   sample_depth      the oracle's depth there (float64)
+  merge_t, merge_maps  for every merge, the label each seeding component
+                    belongs to after it (seeding label -> label), so a
+                    partition that differs can be traced to the merge and the
+                    components where it first differs
 
 Nothing here comes from the CUDA path.  Usage:
     python tests/golden/make_oracle_digest.py c5 [--workers N] [--samples S]
@@ -72,6 +76,13 @@ def main():
     rng = np.random.default_rng(SAMPLE_SEED)
     idx = np.sort(rng.choice(valid, size=min(args.samples, valid.size), replace=False)).astype(np.int32)
     depth = np.asarray(ref["depth"], np.float64).reshape(-1)
+    lab0 = np.asarray(ref["labels0"]).reshape(-1)
+    first = np.full(int(ref["K0"]), lab0.size, np.int64)
+    v0 = lab0 >= 0
+    np.minimum.at(first, lab0[v0], np.nonzero(v0)[0])
+    merge_t = np.array([m["t"] for m in ref["merges"]], np.int32)
+    merge_maps = (np.stack([np.asarray(m["labels"]).reshape(-1)[first] for m in ref["merges"]]).astype(np.int32)
+                  if ref["merges"] else np.zeros((0, int(ref["K0"])), np.int32))
     meta = {"workload": w.name, "config": args.config, "H": H, "W": W, "params": w.params,
             "camera": w.camera, "oracle_seconds": t_oracle, "generate_seconds": t_gen,
             "workers": args.workers, "host": platform.machine(), "cpu_count": os.cpu_count(),
@@ -83,7 +94,8 @@ def main():
         K0=int(ref["K0"]), labels0_sha256=labels_sha256(ref["labels0"]),
         K=int(ref["K"]), labels_sha256=labels_sha256(ref["labels"]),
         iters=int(ref["iters"]), energies=np.asarray(ref["energies"], np.float64),
-        sample_idx=idx, sample_island=isl.reshape(-1)[idx].astype(np.int32), sample_depth=depth[idx])
+        sample_idx=idx, sample_island=isl.reshape(-1)[idx].astype(np.int32), sample_depth=depth[idx],
+        merge_t=merge_t, merge_maps=merge_maps)
     print(json.dumps(dict(meta, K0=int(ref["K0"]), K=int(ref["K"]), iters=int(ref["iters"]))))
 
 
