@@ -658,7 +658,9 @@ extern "C" ni_status ni_load_net(ni_handle* h, const char* path) {
   if (!ok) return ni_fail(h, NI_ERR_INVALID_ARG, std::string("malformed network file ") + path);
   if (h->net) ni_cnn_destroy(h->net);
   h->net = nullptr;
-  ni_status rc = ni_cnn_create(16, hdr[1], 0, &h->net);
+  // tiles per forward launch: the whole map up to 64 tiles (fewer, longer launches)
+  const int nt = ((h->W + hdr[1] - 1) / hdr[1]) * ((h->H + hdr[1] - 1) / hdr[1]);
+  ni_status rc = ni_cnn_create(std::max(1, std::min(nt, 64)), hdr[1], 0, &h->net);
   if (rc != NI_OK) return ni_fail(h, rc, "network allocation");
   rc = ni_cnn_set_params(h->net, buf.data());
   if (rc != NI_OK) return ni_fail(h, rc, "network upload");

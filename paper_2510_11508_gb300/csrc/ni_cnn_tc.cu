@@ -2,23 +2,27 @@
 // tensor cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory).
 // Not in the paper: the network is an extension beyond it.
 //
-// Implicit GEMM per work item = 128 consecutive output pixels of one row:
-//   D[m][co] = sum_{dy, dx, ci} in[y + dy][x0 + m + dx][ci] * w[dy, dx][co][ci]
+// Output pixels are numbered with the input's row pitch, p = y Wi + x (the two
+// columns x >= Wo of every row are computed and dropped), so that the input
+// pixel of tap (dy, dx) is p + dy Wi + dx for every p: linear in p across rows.
+// Implicit GEMM per work item = 128 consecutive p of one image:
+//   D[m][co] = sum_{dy, dx, ci} in[p0 + m + dy Wi + dx][ci] * w[dy, dx][co][ci]
 // M = 128 pixels (the TMEM lanes), N = CO output channels, K = 9 taps x CI.
 //   * A (pixels x channels, K-major) is staged in shared memory once per dy:
-//     the 130 input pixels x0 .. x0 + 129 of row y + dy, stored as the
+//     the 130 input pixels p0 + dy Wi .. p0 + dy Wi + 129, stored as the
 //     no-swizzle canonical layout with 8-row groups 128 B apart (SBO) and the
 //     16-byte channel chunks of all 130 rows 130 x 16 B apart (LBO).  The
 //     views for dx = 0, 1, 2 are the same bytes with the descriptor's start
-//     advanced by dx rows (16 B), so one load of three rows feeds all 9 taps.
+//     advanced by dx rows (16 B), so one load of 3 x 130 pixels feeds all 9 taps.
 //   * B (channels x taps, K-major per output channel) lives in shared memory
 //     for the whole launch.
 //   * One thread issues the 9 x CI/16 MMAs of an item into a TMEM accumulator
 //     of CO columns and commits them to an mbarrier; the four warps then read
 //     their 32 TMEM lanes (pixels) with tcgen05.ld and run the epilogue (bias
 //     and ReLU, the linear last layer, or the ReLU mask of the gradient).
-//   * The next item's rows are loaded by cp.async while the MMAs run (two
-//     staging buffers).
+//   * Two staging buffers and two accumulators: while the epilogue of item j
+//     runs, the MMAs of item j + 1 and the cp.async loads of item j + 2 are
+//     in flight.
 // Every wait on the mbarrier is bounded; on a timeout the CTA flags
 // NI_DEV_ERR_TIMEOUT, stops issuing, waits (bounded) for what it issued, frees
 // its tensor memory and returns.
@@ -139,17 +143,19 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const bf16* __restrict__
   constexpr uint32_t LBO_B = CO * 16;              // between channel chunks of one tap's weights
   constexpr uint32_t TAP_B = KC * LBO_B;
   constexpr uint32_t idesc = idesc_bf16(TC_M, CO);
+  constexpr uint32_t TCOLS = 2 * CO < 32 ? 32 : 2 * CO;   // two accumulators of CO columns
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* bsm = smem;                                  // weights: 9 taps
   unsigned char* asm0 = smem + ((9 * TAP_B + 1023) & ~1023u); // two staging buffers
-  __shared__ uint64_t bar;
+  __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Ho = Hi - 2, Wi = Hi, Wo = Ho;
-  const int nseg = (Wo + TC_M - 1) / TC_M;
-  const long long items = (long long)B * Ho * nseg;
+  const int per_img = (Ho * Wi + TC_M - 1) / TC_M;   // items of one image
+  const long long items = (long long)B * per_img;
+  const long long img_in = (long long)Hi * Wi;
 
   // weights -> shared memory, chunk k of tap t, output channel n at t * TAP_B + k * LBO_B + n * 16
   for (int i = tid; i < 9 * CO * KC; i += TC_THREADS) {
@@ -160,11 +166,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const bf16* __restrict__
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&tmem_base)), "r"(CO < 32 ? 32 : CO) : "memory");
+                 :: "r"(smem_u32(&tmem_base)), "r"(TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -173,72 +180,86 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const bf16* __restrict__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
-  // stage the three input rows of an item into buffer sb
+  // stage the 3 x 130 input pixels of an item into buffer sb (zeros past the image)
   auto stage = [&](long long item, int sb) {
-    const int seg = (int)(item % nseg);
-    const long long ny = item / nseg;
-    const int y = (int)(ny % Ho), n = (int)(ny / Ho);
-    const int x0 = seg * TC_M;
+    const long long n = item / per_img;
+    const int p0 = (int)(item % per_img) * TC_M;
     const uint32_t base = smem_u32(asm0 + sb * STAGE_BYTES);
     for (int i = tid; i < 3 * TC_ROWS * KC; i += TC_THREADS) {
       const int k = i % KC, m = (i / KC) % TC_ROWS, dy = i / (KC * TC_ROWS);
-      const bool ok = x0 + m < Wi;
-      const bf16* src = in + (((long long)n * Hi + y + dy) * Wi + (ok ? x0 + m : 0)) * CI + k * 8;
+      const int q = p0 + dy * Wi + m;
+      const bool ok = q < img_in;
+      const bf16* src = in + (n * img_in + (ok ? q : 0)) * CI + k * 8;
       cp16(base + dy * ROW_BYTES + k * LBO_A + m * 16, src, ok);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
-  uint32_t parity = 0;
-  int sb = 0;
+  // thread 0: the 9 x CI/16 MMAs of the item staged in buffer sb, into accumulator ab
+  auto issue = [&](int sb, int ab) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t a0 = smem_u32(asm0 + sb * STAGE_BYTES), b0 = smem_u32(bsm);
+    int acc = 0;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3, dx = t % 3;
+#pragma unroll
+      for (int ks = 0; ks < CI / 16; ++ks) {
+        const uint64_t ad = sdesc(a0 + dy * ROW_BYTES + dx * 16 + ks * 2 * LBO_A, LBO_A, 128);
+        const uint64_t bd = sdesc(b0 + t * TAP_B + ks * 2 * LBO_B, LBO_B, 128);
+        mma_issue(tmem + ab * CO, ad, bd, idesc, acc);
+        acc = 1;
+      }
+    }
+    mma_commit(&bar[ab]);
+  };
+
+  // Pipeline: item j lives in staging buffer j & 1 and accumulator j & 1.  While
+  // the epilogue of item j runs, the MMAs of item j + 1 and the loads of item
+  // j + 2 are in flight.
+  const long long step = gridDim.x;
+  uint32_t ph0 = 0u, ph1 = 0u;   // phase parity of bar[0], bar[1]
   long long item = blockIdx.x;
-  if (item < items) stage(item, 0);
-  for (; item < items; item += gridDim.x) {
+  if (item < items) {
+    stage(item, 0);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // cp.async writes -> the MMA's reads
     __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(asm0 + sb * STAGE_BYTES), b0 = smem_u32(bsm);
-      int acc = 0;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int dy = t / 3, dx = t % 3;
-#pragma unroll
-        for (int ks = 0; ks < CI / 16; ++ks) {
-          const uint64_t ad = sdesc(a0 + dy * ROW_BYTES + dx * 16 + ks * 2 * LBO_A, LBO_A, 128);
-          const uint64_t bd = sdesc(b0 + t * TAP_B + ks * 2 * LBO_B, LBO_B, 128);
-          mma_issue(tmem, ad, bd, idesc, acc);
-          acc = 1;
-        }
-      }
-      mma_commit(&bar);
-    }
-    // the next item's rows load while the MMAs run
-    const long long nxt = item + gridDim.x;
-    if (nxt < items) stage(nxt, sb ^ 1);
-    const bool ok = mbar_wait(&bar, parity);
+    if (tid == 0) issue(0, 0);
+    if (item + step < items) stage(item + step, 1);
+  }
+  for (int j = 0; item < items; item += step, ++j) {
+    const int b = j & 1;
+    const long long nxt = item + step;
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (nxt < items && tid == 0) issue(b ^ 1, b ^ 1);
+    const uint32_t pb = b ? ph1 : ph0;
+    const bool ok = mbar_wait(&bar[b], pb);
     if (!ok) {
       if (tid == 0) atomicOr(err, NI_DEV_ERR_TIMEOUT);
       s_fail = 1;
     }
     __syncthreads();
-    if (s_fail) {
-      mbar_wait(&bar, parity);   // once more, bounded, for the MMAs in flight
+    if (s_fail) {   // once more, bounded, for the MMAs in flight
+      mbar_wait(&bar[b], pb);
+      if (nxt < items) mbar_wait(&bar[b ^ 1], b ? ph0 : ph1);
       break;
     }
-    parity ^= 1;
+    if (b) ph1 ^= 1u; else ph0 ^= 1u;
+    // item j's staging buffer is free: load item j + 2 into it
+    if (nxt + step < items) stage(nxt + step, b);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // epilogue: warp w owns TMEM lanes (pixels) 32 w .. 32 w + 31
     float v[CO];
-    tmem_ld<CO>(tmem + ((uint32_t)(warp * 32) << 16), v);
+    tmem_ld<CO>(tmem + ((uint32_t)(warp * 32) << 16) + b * CO, v);
     {
-      const int seg = (int)(item % nseg);
-      const long long ny = item / nseg;
-      const int y = (int)(ny % Ho), n = (int)(ny / Ho);
-      const int x = seg * TC_M + warp * 32 + lane;
-      if (x < Wo) {
-        const long long px = ((long long)n * Ho + y) * Wo + x;
+      const long long n = item / per_img;
+      const int p = (int)(item % per_img) * TC_M + warp * 32 + lane;
+      const int y = p / Wi, x = p % Wi;
+      if (y < Ho && x < Wo) {
+        const long long px = (n * Ho + y) * Wo + x;
         if constexpr (MODE == 0) {
           uint32_t pk[CO / 2];
 #pragma unroll
@@ -267,15 +288,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const bf16* __restrict__
         }
       }
     }
-    // the accumulator is rewritten by the next item's MMAs
+    // accumulator b is rewritten by the MMAs of item j + 2
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    sb ^= 1;
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(CO < 32 ? 32 : CO)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TCOLS)
                  : "memory");
 }
 
@@ -292,10 +312,11 @@ cudaError_t launch(const bf16* in, int B, int Hi, const bf16* w, const float* bi
     attr = true;
   }
   const int Ho = Hi - 2;
-  const long long items = (long long)B * Ho * ((Ho + TC_M - 1) / TC_M);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<CI, CO, WCO, MODE>, TC_THREADS, smem);
-  const long long cap = (long long)num_sms * std::max(1, std::min(per_sm, 4));
+  const long long items = (long long)B * ((Ho * Hi + TC_M - 1) / TC_M);
+  // persistent CTAs: as many as shared memory lets one SM hold (CTAs beyond the
+  // resident ones simply wait for a slot)
+  const int per_sm = std::max(1, std::min(4, (int)((227 * 1024) / (smem + 2048))));
+  const long long cap = (long long)num_sms * per_sm;
   const int grid = (int)std::max(1LL, std::min(items, cap));
   k_conv_tc<CI, CO, WCO, MODE><<<grid, TC_THREADS, smem, s>>>(in, B, Hi, w, bias, nbias, out, act_mask, err);
   return cudaGetLastError();
