@@ -74,6 +74,7 @@ class Params:
     n_fill_irls: int = 1
     hard_outliers: bool = False
     connectivity: int = 4
+    bini_residual: bool = False
 
     @staticmethod
     def from_dict(d):
@@ -201,7 +202,7 @@ def sigmoid(x, k=1.0):
         return 1.0 / (1.0 + np.exp(-k * np.asarray(x, np.float64)))
 
 
-def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
+def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None, omega_of=None):
     """Directed BiNI weight W_{b->a} = gamma_{b->a}^2 * w^BiNI_{b->a}
     (Sec. 3.1, Eqs. 4-5):
         w^BiNI_{b->a} = sigma_k( gamma^2 ((z~_{-b} - z~_a)^2 - (z~_b - z~_a)^2) ),
@@ -212,6 +213,15 @@ def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
     is taken as 0.
     a, b: endpoints with b = a + step(d) or b = a - step(d); the opposite
     neighbour is a - (b - a).
+
+    Residual-based variant (omega_of given; the outlier-reweighting ablation's
+    family of variants, Sec. 3.1 read with the residual chi of Eq. 4 in place
+    of the raw log-depth difference):
+        w^BiNI_{b->a} = sigma_k( gamma^2 (chi_{-b->a}^2 - chi_{b->a}^2) ),
+        chi_{c->a} = z~_a - z~_c - w~_{c->a},
+    so that a smooth but steep surface, whose raw differences are large on
+    both sides, is not mistaken for a discontinuity.  omega_of(a, c, d) gives
+    w~_{c->a} for pixels a, c along direction d.
     Pinned: limits and worked values of the sigmoid form, the opposite
     neighbour on each side, and the same-component branch
     (tests/test_oracle_pins.py, tests/test_oracle_scale_rows_pins.py).
@@ -228,8 +238,14 @@ def bini_weight(zt, gam, a, b, d, H, W, valid, k, same_component=None):
     ok = inside & valid[obc]
     if same_component is not None:
         ok &= same_component[obc] == same_component[a]
-    opp = np.where(ok, (zt[obc] - zt[a]) ** 2, 0.0)
-    x = gam * gam * (opp - (zt[b] - zt[a]) ** 2)
+    if omega_of is None:
+        opp = np.where(ok, (zt[obc] - zt[a]) ** 2, 0.0)
+        x = gam * gam * (opp - (zt[b] - zt[a]) ** 2)
+    else:
+        chi_o = zt[a] - zt[obc] - omega_of(a, obc, d)
+        chi_b = zt[a] - zt[b] - omega_of(a, b, d)
+        opp = np.where(ok, chi_o ** 2, 0.0)
+        x = gam * gam * (opp - chi_b ** 2)
     return gam * gam * sigmoid(x, k)
 
 
@@ -416,6 +432,12 @@ class Geometry:
     gam_ba: np.ndarray   # gamma_{b->a} = f n_a.tau_a per edge
     gam_ab: np.ndarray   # gamma_{a->b} = f n_b.tau_b per edge
     conn: int = 4        # pixel connectivity (4 or 8)
+    normals: Optional[np.ndarray] = None
+    cam: Optional[Camera] = None
+
+    def omega_of(self, a, c, d):
+        """w~_{c->a} (Eq. 3) for pixel pairs a, c = a +- step(d)."""
+        return omega(self.normals, self.cam, self.H, self.W, np.asarray(a), np.asarray(c), np.asarray(d))
 
 
 def geometry(normals, mask, cam: Camera, conn: int = 4) -> Geometry:
@@ -424,16 +446,17 @@ def geometry(normals, mask, cam: Camera, conn: int = 4) -> Geometry:
     return Geometry(H, W, mask.reshape(-1).astype(bool), a, b, d,
                     omega(normals, cam, H, W, a, b, d),
                     gamma(normals, cam, H, W, a, d),
-                    gamma(normals, cam, H, W, b, d), conn)
+                    gamma(normals, cam, H, W, b, d), conn, normals, cam)
 
 
-def intra_system(geo: Geometry, labels, zt, k):
+def intra_system(geo: Geometry, labels, zt, k, residual=False):
     """A_c, b_c, W_c of Eq. 9 stacked over all components (block diagonal):
     two rows per intra-component edge (a, b), one per direction,
         row (b->a): +1 at a, -1 at b, rhs w~_{b->a},         weight W_{b->a}
         row (a->b): +1 at b, -1 at a, rhs w~_{a->b} = -w~_{b->a}, weight W_{a->b}
     with W from the BiNI model (Eq. 5) at the current z~ (Reading: -b restricted
-    to a's component)."""
+    to a's component); residual=True takes the residual-based variant of
+    `bini_weight`."""
     n = geo.H * geo.W
     sel = (labels[geo.a] == labels[geo.b]) & (labels[geo.a] >= 0)
     a, b, om = geo.a[sel], geo.b[sel], geo.omega[sel]
@@ -447,26 +470,31 @@ def intra_system(geo: Geometry, labels, zt, k):
     rhs = np.empty(2 * ne)
     rhs[0::2], rhs[1::2] = om, -om
     w = np.empty(2 * ne)
-    w[0::2] = bini_weight(zt, geo.gam_ba[sel], a, b, geo.d[sel], geo.H, geo.W, geo.valid, k, labels)
-    w[1::2] = bini_weight(zt, geo.gam_ab[sel], b, a, geo.d[sel], geo.H, geo.W, geo.valid, k, labels)
+    of = geo.omega_of if residual else None
+    w[0::2] = bini_weight(zt, geo.gam_ba[sel], a, b, geo.d[sel], geo.H, geo.W, geo.valid, k, labels, of)
+    w[1::2] = bini_weight(zt, geo.gam_ab[sel], b, a, geo.d[sel], geo.H, geo.W, geo.valid, k, labels, of)
     return A, rhs, w
 
 
-def fill_components(geo: Geometry, labels, K, k=2.0, n_irls=1):
+def fill_components(geo: Geometry, labels, K, k=2.0, n_irls=1, residual=False):
     """Fill each component (Sec. 3.3): z~ initialised to 0, then
     z~_c <- cg(A_c^T W_c A_c, A_c^T W_c b_c) for every component independently
     (the blocks of one block-diagonal system).  The oracle computes the result
     CG converges to from z~ = 0, the minimum-norm (zero-mean per component)
     least-squares solution, directly (`solve_min_norm`).  `n_irls` sweeps
     recompute W at the current z~; the paper finds one sweep sufficient.
+    residual=True takes the residual-based BiNI weights in the sweeps after
+    the first (Reading: the first sweep starts from z~ = 0, where the paper's
+    weights are sigma(0) = 1/2; a residual is only defined once a solution
+    exists).
     Returns (z~ [H*W] with NaN at invalid pixels, number of sweeps)."""
     n = geo.H * geo.W
     vidx = np.nonzero(geo.valid)[0]
     zt = np.zeros(n)
     blk = labels[vidx]
     iters = 0
-    for _ in range(max(1, n_irls)):
-        A, rhs, w = intra_system(geo, labels, zt, k)
+    for sweep in range(max(1, n_irls)):
+        A, rhs, w = intra_system(geo, labels, zt, k, residual and sweep > 0)
         Wd = sp.diags(w)
         M = (A.T @ Wd @ A).tocsr()[vidx][:, vidx]
         g = (A.T @ (w * rhs))[vidx]
@@ -482,20 +510,20 @@ def _fill_crops(task):
     task on the crop of its bounding box, every pixel outside the component
     masked out and the principal point shifted by the crop's offset.
     Returns [(component, v0, u0, crop mask, z~ on the crop mask)]."""
-    cam_t, k, n_irls, conn, items = task
+    cam_t, k, n_irls, conn, items, residual = task
     cam = Camera(*cam_t)
     out = []
     for c, v0, u0, ncrop, m in items:
         cc = Camera(cam.camera, cam.fx, cam.fy, cam.cx - u0, cam.cy - v0)
         geo = geometry(ncrop, m.astype(np.uint8), cc, conn)
         lab = np.where(m.reshape(-1), 0, -1).astype(np.int64)
-        z, _ = fill_components(geo, lab, 1, k, n_irls)
+        z, _ = fill_components(geo, lab, 1, k, n_irls, residual)
         out.append((c, v0, u0, m, z.reshape(m.shape)[m]))
     return out
 
 
 def fill_components_by_crops(normals, mask, cam: Camera, labels, K, k=2.0, n_irls=1, conn=4, workers=1,
-                             task_px=1 << 21):
+                             task_px=1 << 21, residual=False):
     """The fill of Sec. 3.3 solved component by component, as the paper does
     (its components are filled independently, in parallel processes).
 
@@ -532,9 +560,9 @@ def fill_components_by_crops(normals, mask, cam: Camera, labels, K, k=2.0, n_irl
         cur.append((c, int(v0[c]), int(u0[c]), np.ascontiguousarray(nrm[sl]), m))
         cur_px += m.size
         if cur_px >= task_px:
-            tasks.append((cam_t, k, n_irls, conn, cur)); cur, cur_px = [], 0
+            tasks.append((cam_t, k, n_irls, conn, cur, residual)); cur, cur_px = [], 0
     if cur:
-        tasks.append((cam_t, k, n_irls, conn, cur))
+        tasks.append((cam_t, k, n_irls, conn, cur, residual))
     zt = np.full(H * W, np.nan)
     zt2 = zt.reshape(H, W)
 
@@ -576,6 +604,7 @@ def scale_system(geo: Geometry, labels, K, zt, t, params: Params, e=None):
     Weights: 1 for t <= 1 (alignment, Sec. 3.4); for t > 1 the BiNI weight W
     (Eq. 5) times W^out (Eq. 11) of |chi^(t-1)|, the residual at the current z~.
     Reading: z~ inside W is the current z~, and -b may be any valid pixel.
+    params.bini_residual takes the residual-based BiNI weights (`bini_weight`).
     Pinned: every row of a 3-component map written out by hand at t = 2
     (tests/test_oracle_scale_rows_pins.py) and the dense least-squares solve
     of the same rows (tests/test_oracle_pins.py)."""
@@ -598,8 +627,9 @@ def scale_system(geo: Geometry, labels, K, zt, t, params: Params, e=None):
     else:
         wo = outlier_weight(np.abs(rho), params.L, params.U, params.hard_outliers)
         w = np.empty(2 * ne)
-        w[0::2] = bini_weight(zt, geo.gam_ba[e], a, b, geo.d[e], geo.H, geo.W, geo.valid, params.k) * wo
-        w[1::2] = bini_weight(zt, geo.gam_ab[e], b, a, geo.d[e], geo.H, geo.W, geo.valid, params.k) * wo
+        of = geo.omega_of if params.bini_residual else None
+        w[0::2] = bini_weight(zt, geo.gam_ba[e], a, b, geo.d[e], geo.H, geo.W, geo.valid, params.k, None, of) * wo
+        w[1::2] = bini_weight(zt, geo.gam_ab[e], b, a, geo.d[e], geo.H, geo.W, geo.valid, params.k, None, of) * wo
     return A, rhs, w, e
 
 
@@ -790,10 +820,10 @@ def integrate(normals, mask, cam, params, record=False, workers=0):
     labels, K = seed_components(normals, mask, params.theta_c_deg, params.connectivity)
     if workers >= 1:
         zt, fill_iters = fill_components_by_crops(normals, mask, cam, labels, K, params.k, params.n_fill_irls,
-                                                  params.connectivity, workers)
+                                                  params.connectivity, workers, residual=params.bini_residual)
     geo = geometry(normals, mask, cam, params.connectivity)
     if workers < 1:
-        zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls)
+        zt, fill_iters = fill_components(geo, labels, K, params.k, params.n_fill_irls, params.bini_residual)
     r = scale_loop(geo, labels, K, zt, params, record)
     out = r["z"].reshape(H, W)
     depth = np.exp(out) if cam.camera == PERSP else out

@@ -9,6 +9,8 @@
   on the wrong side, or dropping W^out from one of the rows fails here.
 * `bini_weight(..., same_component=...)` (Sec. 3.1, Eqs. 4-5, with the fill's
   reading that an opposite neighbour outside a's component counts as absent).
+* the residual-based variant of the BiNI weight: the same rows written out
+  with residuals, and closed forms where the model of continuity is exact.
 """
 import math
 
@@ -62,7 +64,7 @@ def _pix_gamma(n, cam, W, p, horizontal):
     return (cam.fx if horizontal else cam.fy) * float(nn @ tau)
 
 
-def _expected_rows(H, W, n, mask, labels, cam, zt, omega_of, k):
+def _expected_rows(H, W, n, mask, labels, cam, zt, omega_of, k, residual=False):
     """Every inter edge's two rows of Eq. 13 at t >= 2, written out pixel by pixel."""
     valid = mask.reshape(-1) > 0
 
@@ -87,15 +89,27 @@ def _expected_rows(H, W, n, mask, labels, cam, zt, omega_of, k):
                 # row (b->a): the BiNI weight of pixel a, its opposite neighbour a - (b - a)
                 uo, vo = u - du, v - dv
                 ok = 0 <= uo < W and 0 <= vo < H and valid[vo * W + uo]
-                opp = (zt[vo * W + uo] - zt[a]) ** 2 if ok else 0.0
                 ga = _pix_gamma(n, cam, W, a, horizontal)
-                w_ba = ga * ga * _sig(ga * ga * (opp - (zt[b] - zt[a]) ** 2), k) * wo
+                if residual:   # chi_{c->a} = z_a - z_c - w~_{c->a} on both sides
+                    o = vo * W + uo
+                    opp = (zt[a] - zt[o] - omega_of(a, o)) ** 2 if ok else 0.0
+                    main = chi ** 2
+                else:
+                    opp = (zt[vo * W + uo] - zt[a]) ** 2 if ok else 0.0
+                    main = (zt[b] - zt[a]) ** 2
+                w_ba = ga * ga * _sig(ga * ga * (opp - main), k) * wo
                 # row (a->b): the BiNI weight of pixel b, its opposite neighbour b + (b - a)
                 uo, vo = ub + du, vb + dv
                 ok = 0 <= uo < W and 0 <= vo < H and valid[vo * W + uo]
-                opp = (zt[vo * W + uo] - zt[b]) ** 2 if ok else 0.0
                 gb = _pix_gamma(n, cam, W, b, horizontal)
-                w_ab = gb * gb * _sig(gb * gb * (opp - (zt[a] - zt[b]) ** 2), k) * wo
+                if residual:   # chi_{a->b} = z_b - z_a - w~_{a->b} = -chi_{b->a}
+                    o = vo * W + uo
+                    opp = (zt[b] - zt[o] - omega_of(b, o)) ** 2 if ok else 0.0
+                    main = chi ** 2
+                else:
+                    opp = (zt[vo * W + uo] - zt[b]) ** 2 if ok else 0.0
+                    main = (zt[a] - zt[b]) ** 2
+                w_ab = gb * gb * _sig(gb * gb * (opp - main), k) * wo
                 ca, cb = labels[a], labels[b]
                 rows[(a, b)] = (
                     # (+1 at pi(a), -1 at pi(b), rhs w~_{b->a} - (z~_a - z~_b), weight)
@@ -106,16 +120,20 @@ def _expected_rows(H, W, n, mask, labels, cam, zt, omega_of, k):
     return rows
 
 
-@pytest.mark.parametrize("seed,k", [(0, 2.0), (1, 2.0), (2, 1.0)])
-def test_scale_rows_at_t2_written_out_by_hand(seed, k):
+@pytest.mark.parametrize("seed,k,residual", [(0, 2.0, False), (1, 2.0, False), (2, 1.0, False),
+                                             (0, 2.0, True), (3, 1.0, True)])
+def test_scale_rows_at_t2_written_out_by_hand(seed, k, residual):
     H, W, n, mask, labels, cam, zt = _map_3x4(seed)
     geo = O.geometry(n, mask, cam)
     K = 3
-    p = O.Params(k=k)
+    p = O.Params(k=k, bini_residual=residual)
     A, rhs, w, e = O.scale_system(geo, labels, K, zt, 2, p)
-    # w~_{b->a} of an edge, from the oracle's Eq. 3 (pinned on planes)
+    # w~_{c->a} of any neighbouring pair, from the oracle's Eq. 3 (pinned on planes)
     om_map = {(int(geo.a[i]), int(geo.b[i])): float(geo.omega[i]) for i in range(len(geo.a))}
-    exp_rows = _expected_rows(H, W, n, mask, labels, cam, zt, lambda a, b: om_map[(a, b)], k)
+
+    def omega_of(a, c):
+        return om_map[(a, c)] if (a, c) in om_map else -om_map[(c, a)]
+    exp_rows = _expected_rows(H, W, n, mask, labels, cam, zt, omega_of, k, residual)
     # the hand enumeration: 5 inter edges (2 horizontal, 3 vertical)
     assert sorted(exp_rows) == sorted((int(geo.a[i]), int(geo.b[i])) for i in e)
     assert len(exp_rows) == 5
@@ -187,3 +205,52 @@ def test_fill_weights_ignore_opposite_neighbours_in_other_components():
     #             row 2->3 at b = 3 has no opposite neighbour (outside)
     exp = [_sig(-0.09, 2.0), _sig(-0.09, 2.0), _sig(-0.01, 2.0), _sig(-0.01, 2.0)]
     np.testing.assert_allclose(w, exp, rtol=1e-14)
+
+
+def test_residual_bini_weight_is_one_half_where_the_model_is_exact():
+    """Where Eq. 3 is exact every residual chi vanishes, so the residual-based
+    weight is gamma^2 sigma_k(0) = gamma^2 / 2 on every edge with an opposite
+    neighbour, however steep or curved the surface:
+      * a perspective plane (Eq. 3 is exact on planes);
+      * an orthographic paraboloid z = 0.3 u^2 + 0.2 v^2: the orthographic
+        reading of Eq. 3 is the trapezoid rule on the slopes, exact for
+        quadratics.  There the raw-difference form is not 1/2: its two sides
+        differ by the curvature."""
+    from synth import generators as G
+    nrm, mask, z, cam = G.plane_map(6, 7, G.PERSP, normal=(0.6, -0.3, -1.0), d=20.0)
+    geo = O.geometry(nrm, mask, O.Camera.from_dict(cam))
+    zt = np.log(z.reshape(-1))
+    w_res = O.bini_weight(zt, geo.gam_ba, geo.a, geo.b, geo.d, 6, 7, geo.valid, 2.0, None, geo.omega_of)
+    has = np.where(geo.d == 0, geo.a % 7 > 0, geo.a // 7 > 0)
+    np.testing.assert_allclose(w_res[has], 0.5 * geo.gam_ba[has] ** 2, rtol=1e-9)
+    # orthographic paraboloid, float64 normals n ~ (-z_u, -z_v, 1)
+    H, W = 7, 9
+    v, u = np.mgrid[0:H, 0:W].astype(np.float64)
+    zq = 0.3 * u * u + 0.2 * v * v
+    g = np.stack([-0.6 * u, -0.4 * v, np.ones_like(u)], -1)
+    nq = np.zeros((H, W, 4))
+    nq[..., :3] = g / np.linalg.norm(g, axis=-1, keepdims=True)
+    geo = O.geometry(nq, np.ones((H, W), np.uint8), O.Camera(O.ORTHO, 1.0, 1.0, 0.0, 0.0))
+    zt = zq.reshape(-1)
+    w_res = O.bini_weight(zt, geo.gam_ba, geo.a, geo.b, geo.d, H, W, geo.valid, 2.0, None, geo.omega_of)
+    w_raw = O.bini_weight(zt, geo.gam_ba, geo.a, geo.b, geo.d, H, W, geo.valid, 2.0)
+    has = np.where(geo.d == 0, geo.a % W > 0, geo.a // W > 0)
+    half = 0.5 * geo.gam_ba[has] ** 2
+    np.testing.assert_allclose(w_res[has], half, rtol=1e-12)
+    assert np.max(np.abs(w_raw[has] / half - 1.0)) > 0.5
+
+
+def test_residual_fill_sweep_on_a_plane_stays_exact():
+    """A second fill sweep with residual-based weights keeps a plane exact
+    (its residuals are zero, so every weight is gamma^2 / 2 again)."""
+    from synth import generators as G
+    nrm, mask, z, cam = G.plane_map(9, 8, G.PERSP, normal=(0.3, 0.2, -1.0), d=30.0)
+    c = O.Camera.from_dict(cam)
+    geo = O.geometry(nrm, mask, c)
+    lab, K = O.seed_components(nrm, mask, 5.0)
+    z1, _ = O.fill_components(geo, lab, K, 2.0, 1)
+    z2, _ = O.fill_components(geo, lab, K, 2.0, 2, residual=True)
+    zr = np.log(z.reshape(-1))
+    zr = zr - zr.mean()
+    np.testing.assert_allclose(z1, zr, atol=1e-10)
+    np.testing.assert_allclose(z2, zr, atol=1e-10)
