@@ -113,6 +113,10 @@ typedef struct {
                                (hardware cluster barriers, reductions through distributed
                                shared memory), 2 one CTA or a cooperative grid with
                                software barriers */
+  int bini_residual;        /* 1: the BiNI weights (Eqs. 4-5) compare the residuals chi of the
+                               two sides instead of their raw log-depth differences, in the
+                               fill sweeps after the first and in the scale loop (t >= 2);
+                               0 (default): as the paper writes them */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

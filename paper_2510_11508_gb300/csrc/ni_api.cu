@@ -101,6 +101,7 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->mg_coarse_sweeps < 0 || c->mg_coarse_sweeps > 64) { why = "mg_coarse_sweeps in [0, 64]"; return NI_ERR_INVALID_ARG; }
   if (c->fill_kernels != 0 && c->fill_kernels != 1) { why = "fill_kernels must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->scale_solver < 0 || c->scale_solver > 2) { why = "scale_solver must be 0, 1 or 2"; return NI_ERR_INVALID_ARG; }
+  if (c->bini_residual != 0 && c->bini_residual != 1) { why = "bini_residual must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;

@@ -120,39 +120,54 @@ __global__ void k_diag_rhs(const float* __restrict__ wr, const float* __restrict
   }
 }
 
-// BiNI reweighting sweep of the fill (n_fill_irls > 1): directed weights at the
-// current z~ (Eq. 5), the opposite neighbour restricted to the component.
-__device__ __forceinline__ float bini_w(float gam, float za, float zb, float zo, bool has_o, float k) {
-  float g2 = gam * gam;
-  float dop = has_o ? (zo - za) * (zo - za) : 0.f;
-  float arg = g2 * (dop - (zb - za) * (zb - za));
-  return g2 / (1.f + expf(-k * arg));
+// BiNI reweighting sweep of the fill (n_fill_irls > 1): the weight of an edge
+// (a, b) is W_{b->a} + W_{a->b} at the current z~ (Eq. 5), the opposite
+// neighbours oa = a - (b - a) and ob = b + (b - a) counted only inside the
+// component.  om_ab = omega~_{b->a}; om_oa = omega~ stored for the edge (oa, a),
+// which is omega~_{a->oa}; om_ob = omega~ stored for the edge (b, ob), which is
+// omega~_{ob->b}.  res: the two sides compared through their residuals
+// chi_{c->p} = z~_p - z~_c - omega~_{c->p} instead of the raw differences.
+__device__ __forceinline__ float bini_pair(float ga, float gb, float xa, float xb, float xoa, float xob, bool hoa,
+                                           bool hob, float om_ab, float om_oa, float om_ob, int res, float k) {
+  float main2, da, db;
+  if (res) {
+    const float c = xa - xb - om_ab;
+    main2 = c * c;
+    const float ca = xa - xoa + om_oa, cb = xb - xob - om_ob;
+    da = hoa ? ca * ca : 0.f;
+    db = hob ? cb * cb : 0.f;
+  } else {
+    main2 = (xb - xa) * (xb - xa);
+    da = hoa ? (xoa - xa) * (xoa - xa) : 0.f;
+    db = hob ? (xob - xb) * (xob - xb) : 0.f;
+  }
+  const float g2a = ga * ga, g2b = gb * gb;
+  return g2a / (1.f + expf(-k * g2a * (da - main2))) + g2b / (1.f + expf(-k * g2b * (db - main2)));
 }
 
 __global__ void k_fill_reweight(const float* __restrict__ ntau, const int* __restrict__ labels,
-                                const float* __restrict__ x, int H, int W, int persp, float fx,
-                                float fy, float k, float* __restrict__ wr, float* __restrict__ wd) {
+                                const float* __restrict__ x, const float2* __restrict__ omega, int H, int W,
+                                int persp, float fx, float fy, float k, int res, float* __restrict__ wr,
+                                float* __restrict__ wd) {
   const int N = H * W;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     const int la = labels[a];
     const int u = a % W, v = a / W;
     if (la >= 0 && wr[a] > 0.f) {
       const int b = a + 1;
-      float f = persp ? fx : 1.f;
-      float gba = f * ntau[a], gab = f * ntau[b];
-      bool ho_a = (u > 0) && labels[a - 1] == la;
-      bool ho_b = (u + 2 < W) && labels[b + 1] == la;
-      wr[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - 1] : 0.f, ho_a, k) +
-              bini_w(gab, x[b], x[a], ho_b ? x[b + 1] : 0.f, ho_b, k);
+      const float f = persp ? fx : 1.f;
+      const bool ho_a = (u > 0) && labels[a - 1] == la;
+      const bool ho_b = (u + 2 < W) && labels[b + 1] == la;
+      wr[a] = bini_pair(f * ntau[a], f * ntau[b], x[a], x[b], ho_a ? x[a - 1] : 0.f, ho_b ? x[b + 1] : 0.f, ho_a,
+                        ho_b, omega[a].x, ho_a ? omega[a - 1].x : 0.f, ho_b ? omega[b].x : 0.f, res, k);
     }
     if (la >= 0 && wd[a] > 0.f) {
       const int b = a + W;
-      float f = persp ? fy : 1.f;
-      float gba = f * ntau[a], gab = f * ntau[b];
-      bool ho_a = (v > 0) && labels[a - W] == la;
-      bool ho_b = (v + 2 < H) && labels[b + W] == la;
-      wd[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W] : 0.f, ho_a, k) +
-              bini_w(gab, x[b], x[a], ho_b ? x[b + W] : 0.f, ho_b, k);
+      const float f = persp ? fy : 1.f;
+      const bool ho_a = (v > 0) && labels[a - W] == la;
+      const bool ho_b = (v + 2 < H) && labels[b + W] == la;
+      wd[a] = bini_pair(f * ntau[a], f * ntau[b], x[a], x[b], ho_a ? x[a - W] : 0.f, ho_b ? x[b + W] : 0.f, ho_a,
+                        ho_b, omega[a].y, ho_a ? omega[a - W].y : 0.f, ho_b ? omega[b].y : 0.f, res, k);
     }
   }
 }
@@ -235,10 +250,11 @@ __global__ void k_diag_rhs8(const float* __restrict__ wr, const float* __restric
 }
 
 // BiNI reweighting of the diagonal edges (n_fill_irls > 1); the opposite
-// neighbour of a is a - (b - a), restricted to the component.
+// neighbour of a is a - (b - a), restricted to the component (bini_pair).
 __global__ void k_fill_reweight_diag(const float* __restrict__ ntau, const int* __restrict__ labels,
-                                     const float* __restrict__ x, int H, int W, int persp, float fx, float fy,
-                                     float k, float* __restrict__ wdr, float* __restrict__ wdl) {
+                                     const float* __restrict__ x, const float2* __restrict__ omega_d, int H, int W,
+                                     int persp, float fx, float fy, float k, int res, float* __restrict__ wdr,
+                                     float* __restrict__ wdl) {
   const int N = H * W;
   const float f = persp ? sqrtf(fx * fy) : 1.f;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
@@ -246,19 +262,19 @@ __global__ void k_fill_reweight_diag(const float* __restrict__ ntau, const int* 
     const int u = a % W, v = a / W;
     if (la >= 0 && wdr[a] > 0.f) {
       const int b = a + W + 1;
-      const float gba = f * ntau[a], gab = f * ntau[b];
       const bool ho_a = (u > 0) && (v > 0) && labels[a - W - 1] == la;
       const bool ho_b = (u + 2 < W) && (v + 2 < H) && labels[b + W + 1] == la;
-      wdr[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W - 1] : 0.f, ho_a, k) +
-               bini_w(gab, x[b], x[a], ho_b ? x[b + W + 1] : 0.f, ho_b, k);
+      wdr[a] = bini_pair(f * ntau[a], f * ntau[b], x[a], x[b], ho_a ? x[a - W - 1] : 0.f,
+                         ho_b ? x[b + W + 1] : 0.f, ho_a, ho_b, omega_d[a].x, ho_a ? omega_d[a - W - 1].x : 0.f,
+                         ho_b ? omega_d[b].x : 0.f, res, k);
     }
     if (la >= 0 && wdl[a] > 0.f) {
       const int b = a + W - 1;
-      const float gba = f * ntau[a], gab = f * ntau[b];
       const bool ho_a = (u + 1 < W) && (v > 0) && labels[a - W + 1] == la;
       const bool ho_b = (u >= 2) && (v + 2 < H) && labels[b + W - 1] == la;
-      wdl[a] = bini_w(gba, x[a], x[b], ho_a ? x[a - W + 1] : 0.f, ho_a, k) +
-               bini_w(gab, x[b], x[a], ho_b ? x[b + W - 1] : 0.f, ho_b, k);
+      wdl[a] = bini_pair(f * ntau[a], f * ntau[b], x[a], x[b], ho_a ? x[a - W + 1] : 0.f,
+                         ho_b ? x[b + W - 1] : 0.f, ho_a, ho_b, omega_d[a].y, ho_a ? omega_d[a - W + 1].y : 0.f,
+                         ho_b ? omega_d[b].y : 0.f, res, k);
     }
   }
 }
@@ -1039,11 +1055,13 @@ ni_status fill_solve_launch(ni_handle* h, cudaStream_t s) {
   if (rc != NI_OK) return rc;
   for (int sweep = 0; sweep < std::max(1, h->cfg.n_fill_irls); ++sweep) {
     if (sweep > 0) {
-      k_fill_reweight<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp, h->fx,
-                                                        h->fy, (float)h->cfg.k, h->wr, h->wd); NI_COUNT(h);
+      k_fill_reweight<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->omega, h->H, h->W, h->persp,
+                                                        h->fx, h->fy, (float)h->cfg.k, h->cfg.bini_residual, h->wr,
+                                                        h->wd); NI_COUNT(h);
       if (h->cfg.connectivity == 8) {
-        k_fill_reweight_diag<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->H, h->W, h->persp,
-                                                                h->fx, h->fy, (float)h->cfg.k, h->wdr, h->wdl);
+        k_fill_reweight_diag<<<grid_px(h, h->N), 256, 0, s>>>(h->ntau, h->labels, h->x, h->omega_d, h->H, h->W,
+                                                                h->persp, h->fx, h->fy, (float)h->cfg.k,
+                                                                h->cfg.bini_residual, h->wdr, h->wdl);
         NI_COUNT(h);
         k_diag_rhs8<<<grid_px(h, h->N), 256, 0, s>>>(h->wr, h->wd, h->omega, h->wdr, h->wdl, h->omega_d, h->H,
                                                        h->W, h->invd, h->b); NI_COUNT(h);

@@ -450,7 +450,19 @@ struct EdgeArgs {
   int H, W, persp;
   double fx, fy, k, Lt, Ut, U;
   int hard;
+  int bini_res;            // residual-based BiNI weights
 };
+
+// omega~ stored for the edge (p, p + step(dir)): omega~_{(p + step) -> p}
+template <int CONN>
+__device__ __forceinline__ double edge_omega(const EdgeArgs& A, int p, int dir) {
+  if constexpr (CONN == 8) {
+    const float2 o = dir >= 2 ? A.omega_d[p] : A.omega[p];
+    return (double)((dir & 1) ? o.y : o.x);
+  }
+  const float2 o = A.omega[p];
+  return (double)(dir ? o.y : o.x);
+}
 
 __device__ __forceinline__ double sigm(double x, double k) { return 1.0 / (1.0 + exp(-k * x)); }
 
@@ -508,15 +520,27 @@ __global__ void k_edge_accum(EdgeArgs A) {
         }
         const double gba = f * (double)A.ntau[a], gab = f * (double)A.ntau[b];
         double doa = 0.0, dob = 0.0;
+        // the opposite side of a is the edge (a - step, a), of b the edge (b, b + step)
         if (has_oa) {
           int o = a - step, co = A.labels[o];
-          if (co >= 0) { double zo = (double)A.x[o] + A.soff[co]; doa = (zo - za) * (zo - za); }
+          if (co >= 0) {
+            const double zo = (double)A.x[o] + A.soff[co];
+            // residual chi_{o->a} = z_a - z_o - omega~_{o->a}, omega~_{o->a} = -omega~_{a->o}
+            const double e = A.bini_res ? za - zo + edge_omega<CONN>(A, o, dir) : zo - za;
+            doa = e * e;
+          }
         }
         if (has_ob) {
           int o = b + step, co = A.labels[o];
-          if (co >= 0) { double zo = (double)A.x[o] + A.soff[co]; dob = (zo - zb) * (zo - zb); }
+          if (co >= 0) {
+            const double zo = (double)A.x[o] + A.soff[co];
+            // residual chi_{o->b} = z_b - z_o - omega~_{o->b}
+            const double e = A.bini_res ? zb - zo - edge_omega<CONN>(A, b, dir) : zo - zb;
+            dob = e * e;
+          }
         }
-        const double d2 = (zb - za) * (zb - za);
+        // the edge's own side: raw (z_b - z_a)^2, or its residual chi^2 (the same for both rows)
+        const double d2 = A.bini_res ? rho * rho : (zb - za) * (zb - za);
         const double g2a = gba * gba, g2b = gab * gab;
         const double wba = g2a * sigm(g2a * (doa - d2), A.k);
         const double wab = g2b * sigm(g2b * (dob - d2), A.k);
@@ -1163,6 +1187,7 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   ea.p_acc = h->p_acc; ea.st = st; ea.H = h->H; ea.W = h->W; ea.persp = h->persp;
   ea.fx = h->cfg.cam.fx; ea.fy = h->cfg.cam.fy; ea.k = h->cfg.k;
   ea.Lt = log10(h->cfg.L); ea.Ut = log10(h->cfg.U); ea.U = h->cfg.U; ea.hard = h->cfg.hard_outliers;
+  ea.bini_res = h->cfg.bini_residual;
   if (h->cfg.connectivity == 8) k_edge_accum<8><<<ge, 256, 0, s>>>(ea);
   else k_edge_accum<4><<<ge, 256, 0, s>>>(ea);
   NI_COUNT(h);

@@ -113,3 +113,19 @@ def test_outlier_variants_match_oracle(over):
     np.testing.assert_array_equal(labels, ref["labels"])
     assert err <= 1e-4
     assert mx <= PIXEL_TOL
+
+
+@pytest.mark.parametrize("name,irls", [("c3_small", 1), ("c2", 2)])
+def test_residual_bini_variant_matches_oracle(name, irls):
+    """The residual-based BiNI weights (bini_residual) in the scale loop (and
+    in the second fill sweep) against the oracle's variant."""
+    w, depth, labels, st, ref = _run(name, bini_residual=1, n_fill_irls=irls)
+    zg = np.log(depth) if w.camera["camera"] == 1 else depth
+    err = rel_depth_error(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, w.camera["camera"])
+    mx = rel_depth_max(np.nan_to_num(zg), np.nan_to_num(ref["z"]), w.mask, w.camera["camera"])
+    print(name, "residual BiNI", {k: st[k] for k in ("K0", "K_final", "scale_iters", "merges")}, "oracle", ref["K"],
+          ref["iters"], "err", err, "max", mx)
+    assert st["K_final"] == ref["K"] and st["scale_iters"] == ref["iters"]
+    np.testing.assert_array_equal(labels, ref["labels"])
+    assert err <= 1e-4
+    assert mx <= PIXEL_TOL

@@ -163,3 +163,27 @@ def test_multigrid_mean_projection_option(name):
     scale = 1.0 if w.camera["camera"] == 1 else float(np.ptp(w.depth_gt[w.mask > 0]))
     assert float(np.sqrt(np.mean(d * d))) / scale <= 1e-4
     assert float(np.abs(d).max()) / scale <= PIXEL_TOL
+
+
+@pytest.mark.parametrize("batched,precond", [(0, 0), (1, 0), (1, 1)])
+def test_fill_residual_bini_sweep_matches_oracle(batched, precond):
+    """A second fill sweep with the residual-based BiNI weights (bini_residual)."""
+    w = make_workload("c3_small")
+    p = dict(w.params, n_fill_irls=2)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    it = integrator(H, W, w.camera, p, batched=batched, precond=precond, bini_residual=1)
+    it.seed_components(n, m)
+    z = it.solve_components().cpu().numpy()
+    cam = O.Camera.from_dict(w.camera)
+    geo = O.geometry(w.normals, w.mask, cam)
+    lab, K = O.seed_components(w.normals, w.mask, p["theta_c_deg"])
+    zr, _ = O.fill_components(geo, lab, K, p.get("k", 2.0), 2, residual=True)
+    zr = np.nan_to_num(zr).reshape(H, W)
+    zraw, _ = O.fill_components(geo, lab, K, p.get("k", 2.0), 2)
+    d = (z - zr)[w.mask > 0]
+    sep = float(np.abs(np.nan_to_num(zraw).reshape(H, W) - zr)[w.mask > 0].max())
+    print("residual sweep rms", float(np.sqrt(np.mean(d * d))), "max", float(np.abs(d).max()),
+          "raw vs residual oracle max", sep)
+    assert np.sqrt(np.mean(d * d)) < 1e-4
+    assert float(np.abs(d).max()) <= PIXEL_TOL
