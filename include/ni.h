@@ -259,6 +259,20 @@ ni_status ni_min_made(ni_handle* h, const float* z, int z_is_log, const int32_t*
  * NI_ERR_INVALID_ARG if the file is missing or malformed. */
 ni_status ni_load_net(ni_handle* h, const char* path);
 
+/* Tuning table (not in the paper: launch shapes and preconditioner knobs of
+ * this implementation).  A text file written by the package's tuner
+ * (paper_2510_11508_gb300/tune.py): one row per line,
+ *     max_px  max_k0  ctas_per_sm  mg_cta_cells  mg_omega  scale_solver
+ * ('#' starts a comment).  From then on, every ni_solve_components (and
+ * ni_integrate*) gives each of those four knobs that the handle's ni_config
+ * left at 0 the value of the first row with H * W <= max_px and K0 (the
+ * components after seeding) <= max_k0; with no such row, or for knobs set in
+ * the config, nothing changes.  The knobs change speed, not the answer: the
+ * tuner keeps only values whose result equals the default configuration's.
+ * NI_ERR_INVALID_ARG if the file is missing or malformed (the previous table,
+ * if any, stays).  Host only. */
+ni_status ni_load_tuning(ni_handle* h, const char* path);
+
 /* Seeding without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory while they
  * run -- for example a real-time pipeline that reserves all memory at start-up,

@@ -190,6 +190,7 @@ extern "C" ni_status ni_create(const ni_config* cfg, ni_handle** out) {
   if (check_config(cfg, why) != NI_OK) return NI_ERR_INVALID_ARG;
   ni_handle* h = new ni_handle();
   h->cfg = *cfg;
+  h->cfg_user = *cfg;
   h->H = cfg->H;
   h->W = cfg->W;
   h->N = cfg->H * cfg->W;
@@ -326,9 +327,52 @@ extern "C" ni_status ni_seed_components(ni_handle* h, const float* normals, cons
   return ni_cuda_check(h, cudaStreamSynchronize(s), "seeding");
 }
 
+// The knobs the caller left at 0 (auto) take the first tuning-table row that
+// covers this map's grid pixels and its number of components after seeding.
+static void apply_tuning(ni_handle* h) {
+  if (h->tune.empty()) return;
+  const TuneRow* r = nullptr;
+  for (const TuneRow& t : h->tune)
+    if ((long long)h->N <= t.max_px && (long long)h->K_host <= t.max_k0) { r = &t; break; }
+  const ni_config& u = h->cfg_user;
+  h->cfg.ctas_per_sm = (r && u.ctas_per_sm == 0) ? r->ctas_per_sm : u.ctas_per_sm;
+  h->cfg.mg_cta_cells = (r && u.mg_cta_cells == 0) ? r->mg_cta_cells : u.mg_cta_cells;
+  h->cfg.mg_omega = (r && u.mg_omega == 0) ? r->mg_omega : u.mg_omega;
+  h->cfg.scale_solver = (r && u.scale_solver == 0) ? r->scale_solver : u.scale_solver;
+}
+
+extern "C" ni_status ni_load_tuning(ni_handle* h, const char* path) {
+  if (!h) return NI_ERR_INVALID_ARG;
+  if (!path) return ni_fail(h, NI_ERR_INVALID_ARG, "path is required");
+  FILE* f = fopen(path, "r");
+  if (!f) return ni_fail(h, NI_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  std::vector<TuneRow> rows;
+  char line[512];
+  bool ok = true;
+  while (fgets(line, sizeof line, f)) {
+    const char* p = line;
+    while (*p == ' ' || *p == '\t') ++p;
+    if (*p == '#' || *p == '\n' || *p == '\0') continue;
+    TuneRow t;
+    if (sscanf(p, "%lld %lld %d %d %lf %d", &t.max_px, &t.max_k0, &t.ctas_per_sm, &t.mg_cta_cells, &t.mg_omega,
+               &t.scale_solver) != 6 ||
+        t.max_px < 1 || t.max_k0 < 1 || t.ctas_per_sm < 0 || t.ctas_per_sm > 8 || t.mg_cta_cells < 0 ||
+        !(t.mg_omega >= 0 && t.mg_omega < 1) || t.scale_solver < 0 || t.scale_solver > 2) {
+      ok = false;
+      break;
+    }
+    rows.push_back(t);
+  }
+  fclose(f);
+  if (!ok || rows.empty()) return ni_fail(h, NI_ERR_INVALID_ARG, std::string("malformed tuning table ") + path);
+  h->tune = rows;
+  return NI_OK;
+}
+
 extern "C" ni_status ni_solve_components(ni_handle* h, float* logdepth_out, ni_stream_t stream) {
   if (!h) return NI_ERR_INVALID_ARG;
   if (h->stage < 1) return ni_fail(h, NI_ERR_STATE, "ni_solve_components before ni_seed_components");
+  apply_tuning(h);
   if (h->cfg.warm_start && !h->net)
     return ni_fail(h, NI_ERR_NO_NET, "warm start requested but no network is loaded");
   cudaStream_t s = (cudaStream_t)stream;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/ni.h"
 
@@ -72,8 +73,21 @@ struct DevState {
 
 struct ni_cnn;
 
+// One row of a tuning table (ni_load_tuning): the knobs for maps of at most
+// max_px grid pixels and max_k0 components after seeding.
+struct TuneRow {
+  long long max_px;
+  long long max_k0;
+  int ctas_per_sm;
+  int mg_cta_cells;
+  double mg_omega;
+  int scale_solver;
+};
+
 struct ni_handle {
   ni_config cfg;
+  ni_config cfg_user;          // the configuration as given: 0 knobs are the tuning table's to set
+  std::vector<TuneRow> tune;
   int dev = 0;
   int num_sms = 0;
   int scale_cluster = -1;      // CTAs of the cluster-mode scale PCG (-1 not yet queried, 0 unavailable)

@@ -23,7 +23,7 @@ STATUS = {0: "NI_OK", 1: "NI_ERR_INVALID_ARG", 2: "NI_ERR_CUDA", 3: "NI_ERR_OOM"
 EXPORTS = ["ni_config_default", "ni_create", "ni_destroy", "ni_seed_components",
            "ni_solve_components", "ni_solve_scales", "ni_merge", "ni_merge_residuals",
            "ni_integrate", "ni_integrate_host", "ni_get_logdepth", "ni_load_net", "ni_last_error",
-           "ni_status_string", "ni_seed_components_noalloc", "ni_min_made"]
+           "ni_status_string", "ni_seed_components_noalloc", "ni_min_made", "ni_load_tuning"]
 
 
 class Camera(C.Structure):
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = False):
     L.ni_seed_components_noalloc.argtypes = [vp, vp, C.c_int, C.c_int, C.POINTER(Camera), C.c_double,
                                              vp, vp, vp]
     L.ni_load_net.argtypes = [vp, C.c_char_p]
+    L.ni_load_tuning.argtypes = [vp, C.c_char_p]
     L.ni_min_made.argtypes = [vp, vp, C.c_int, vp, C.c_int32, vp, C.POINTER(C.c_double), vp, vp, vp]
     L.ni_last_error.argtypes = [vp]
     L.ni_last_error.restype = C.c_char_p
@@ -116,6 +117,11 @@ class NIError(RuntimeError):
 def default_net_path() -> str:
     """The trained warm-start network shipped with the package."""
     return os.path.join(os.path.dirname(os.path.abspath(__file__)), "nets", "warmstart_256.bin")
+
+
+def default_tuning_path() -> str:
+    """The tuning table written by tune.py on GB300 and shipped with the package."""
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning", "gb300.txt")
 
 
 def default_config(H: int, W: int) -> Config:
@@ -263,6 +269,12 @@ class Integrator:
                                              depth_out.data_ptr(), C.byref(st), _stream()),
                     (NI_ERR_NOT_CONVERGED,) if allow_unconverged else ())
         return st.as_dict()
+
+    def load_tuning(self, path: Optional[str] = None):
+        """Knobs left at 0 in the config come from the tuning table at `path`
+        (default: the table shipped for GB300) for every later map."""
+        path = default_tuning_path() if path is None else path
+        self._raise(self.L.ni_load_tuning(self.h, path.encode()))
 
     def load_net(self, path: str):
         self._raise(self.L.ni_load_net(self.h, path.encode()))

@@ -1,6 +1,7 @@
-"""Autotuner of the fill's launch shape and multigrid knobs.
+"""Autotuner of the launch shapes and preconditioner knobs, and the tuning
+table the library reads at run time (ni_load_tuning).
 
-Runs ni_integrate on a caller's map for every point of a small search space and
+Runs ni_integrate on a map for every point of a small search space and
 returns the configuration with the lowest median time whose labels are equal to
 the reference configuration's and whose log-depth agrees with it to `rtol`
 (the tuner never trades accuracy for speed).  Knobs:
@@ -10,9 +11,15 @@ the reference configuration's and whose log-depth agrees with it to `rtol`
   mg_cta_cells      coarse-level cells per CTA of a multigrid pass (a pass syncs
                     only its CTAs: fewer barrier arrivals vs. serial work);
   mg_omega          damped-Jacobi weight of the V-cycle smoother;
-  mg_correction     scale of the coarse-grid correction.
+  scale_solver      relative-scale PCG in one thread-block cluster (1) or a
+                    cooperative grid (2).
+
+`--write PATH` tunes a list of maps of growing size and writes one table row
+per map, keyed by its grid pixels and its components after seeding; the
+library then picks the knobs of the first row that covers a new map:
 
     python -m paper_2510_11508_gb300.tune --workload c3
+    python -m paper_2510_11508_gb300.tune --write table.txt --workloads c2,c3,c4_eval,c5
 """
 from __future__ import annotations
 
@@ -29,10 +36,12 @@ from . import ni
 
 SPACE = {
     "ctas_per_sm": [2, 4],
-    "mg_cta_cells": [128, 256, 512],
-    "mg_omega": [0.8, 0.9, 0.95],
-    "mg_correction": [1.0],
+    "mg_cta_cells": [256, 512],
+    "mg_omega": [0.85, 0.9, 0.95],
+    "scale_solver": [1, 2],
 }
+# the library's defaults of the same knobs (what a 0 in the config means)
+DEFAULTS = {"ctas_per_sm": 4, "mg_cta_cells": 256, "mg_omega": 0.9, "scale_solver": 0}
 
 
 def _time(it, n, m, reps):
@@ -76,7 +85,21 @@ def tune(normals: torch.Tensor, mask: torch.Tensor, camera: Dict, params: Option
         if ok and ms < best_ms:
             best, best_ms = knobs, ms
     log(f"default {ms0:.3f} ms -> best {best_ms:.3f} ms with {best}")
-    return best, table
+    return best, table, ms0, best_ms, s0
+
+
+def write_table(path: str, rows, log=print):
+    """rows: (max_px, max_k0, knobs) in increasing max_px; a last catch-all row
+    keeps the defaults."""
+    with open(path, "w") as f:
+        f.write("# tuning table of libni (ni_load_tuning), written by paper_2510_11508_gb300.tune\n")
+        f.write("# max_px max_k0 ctas_per_sm mg_cta_cells mg_omega scale_solver\n")
+        for max_px, max_k0, knobs, note in rows:
+            k = dict(DEFAULTS, **knobs)
+            f.write(f"{max_px} {max_k0} {k['ctas_per_sm']} {k['mg_cta_cells']} {k['mg_omega']} "
+                    f"{k['scale_solver']}  # {note}\n")
+        f.write(f"{1 << 40} {1 << 40} 0 0 0 0  # anything larger: the built-in defaults\n")
+    log(f"wrote {path}")
 
 
 def main():
@@ -86,12 +109,29 @@ def main():
     from synth import make_workload
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c3")
+    ap.add_argument("--workloads", default="c2,c3,c4_eval,c5")
+    ap.add_argument("--write", default=None, help="tune every map of --workloads and write the table here")
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args()
-    w = make_workload(a.workload)
-    n = torch.from_numpy(w.normals).cuda()
-    m = torch.from_numpy(w.mask).cuda()
-    tune(n, m, w.camera, w.params, reps=a.reps)
+    if a.write is None:
+        w = make_workload(a.workload)
+        n = torch.from_numpy(w.normals).cuda()
+        m = torch.from_numpy(w.mask).cuda()
+        tune(n, m, w.camera, w.params, reps=a.reps)
+        return
+    rows = []
+    for name in a.workloads.split(","):
+        w = make_workload(name)
+        n = torch.from_numpy(w.normals).cuda()
+        m = torch.from_numpy(w.mask).cuda()
+        best, _, ms0, ms1, s0 = tune(n, m, w.camera, w.params, reps=a.reps)
+        H, W = w.mask.shape
+        rows.append((H * W, 4 * max(1, s0["K0"]), best,
+                     f"{w.name}: K0 {s0['K0']}, default {ms0:.2f} ms, tuned {ms1:.2f} ms"))
+        del n, m
+        torch.cuda.empty_cache()
+    rows.sort(key=lambda r: r[0])
+    write_table(a.write, rows)
 
 
 if __name__ == "__main__":
