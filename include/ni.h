@@ -117,6 +117,11 @@ typedef struct {
                                two sides instead of their raw log-depth differences, in the
                                fill sweeps after the first and in the scale loop (t >= 2);
                                0 (default): as the paper writes them */
+  int learned_weights;      /* 1 (needs warm_start): the two alignment iterations (t <= 1) of the
+                               relative-scale loop weight each inter-edge row by the network's
+                               predicted continuity of the edge (its estimate of w^BiNI, Eq. 4,
+                               floored at 1e-3) instead of 1; 0 (default): uniform, as the
+                               paper's alignment */
 } ni_config;
 
 /* Per-run statistics (host struct filled by ni_integrate / ni_integrate_host). */

@@ -102,6 +102,8 @@ static ni_status check_config(const ni_config* c, std::string& why) {
   if (c->fill_kernels != 0 && c->fill_kernels != 1) { why = "fill_kernels must be 0 or 1"; return NI_ERR_INVALID_ARG; }
   if (c->scale_solver < 0 || c->scale_solver > 2) { why = "scale_solver must be 0, 1 or 2"; return NI_ERR_INVALID_ARG; }
   if (c->bini_residual != 0 && c->bini_residual != 1) { why = "bini_residual must be 0 or 1"; return NI_ERR_INVALID_ARG; }
+  if (c->learned_weights != 0 && c->learned_weights != 1) { why = "learned_weights must be 0 or 1"; return NI_ERR_INVALID_ARG; }
+  if (c->learned_weights && !c->warm_start) { why = "learned_weights needs warm_start = 1"; return NI_ERR_INVALID_ARG; }
   if (c->mg_cta_cells < 0) { why = "mg_cta_cells must be >= 0"; return NI_ERR_INVALID_ARG; }
   if (c->warm_start && !c->batched) { why = "warm_start needs the batched fill (batched = 1)"; return NI_ERR_INVALID_ARG; }
   return NI_OK;
@@ -257,7 +259,7 @@ extern "C" ni_status ni_destroy(ni_handle* h) {
   dfree(h->invd); dfree(h->x); dfree(h->r); dfree(h->p); dfree(h->p2); dfree(h->q); dfree(h->b);
   dfree(h->blk); dfree(h->d_count); dfree(h->radix_hist); dfree(h->st);
   dfree(h->in_normals); dfree(h->in_mask); dfree(h->out_depth);
-  dfree(h->tile_in); dfree(h->tile_out);
+  dfree(h->tile_in); dfree(h->tile_out); dfree(h->lw);
   free_mg(h);
   free_made(h);
   if (h->net) ni_cnn_destroy(h->net);

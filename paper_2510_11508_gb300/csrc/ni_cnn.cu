@@ -609,14 +609,27 @@ extern "C" ni_status ni_cnn_make_tiles(const float* normals, const uint8_t* mask
 // ---------------------------------------------------------------------------
 // warm start inside the fill: x0 = network log-depth, tile by tile
 // ---------------------------------------------------------------------------
+// x0 = channel 0; with lw, also the continuity of the right, down, left and up
+// edge (sigmoids of channels 1..4: the network's estimate of w^BiNI)
 __global__ void k_scatter_x0(const float* __restrict__ pred, int H, int W, int T, int ntx, const int* __restrict__ labels,
-                             float* __restrict__ x) {
+                             float* __restrict__ x, float4* __restrict__ lw) {
   const int N = H * W;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < N; a += gridDim.x * blockDim.x) {
     const int u = a % W, v = a / W;
     const int t = (v / T) * ntx + (u / T);
     const long long o = (((long long)t * T + (v % T)) * T + (u % T)) * 5;
-    x[a] = labels[a] >= 0 ? pred[o] : 0.f;
+    const bool ok = labels[a] >= 0;
+    x[a] = ok ? pred[o] : 0.f;
+    if (lw) {
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (ok) {
+        q.x = 1.f / (1.f + __expf(-pred[o + 1]));
+        q.y = 1.f / (1.f + __expf(-pred[o + 2]));
+        q.z = 1.f / (1.f + __expf(-pred[o + 3]));
+        q.w = 1.f / (1.f + __expf(-pred[o + 4]));
+      }
+      lw[a] = q;
+    }
   }
 }
 
@@ -639,7 +652,12 @@ ni_status warm_start_launch(ni_handle* h, cudaStream_t s) {
     h->launches += 1 + NL;
     if (rc != NI_OK) return ni_fail(h, rc, "warm-start forward");
   }
-  k_scatter_x0<<<grid_of(h->N, 256), 256, 0, s>>>(h->tile_out, h->H, h->W, T, ntx, h->labels, h->x); NI_COUNT(h);
+  if (h->cfg.learned_weights && !h->lw) {
+    cudaError_t e = cudaMalloc((void**)&h->lw, sizeof(float4) * (size_t)h->N);
+    if (e != cudaSuccess) return ni_cuda_check(h, e, "learned edge weights");
+  }
+  k_scatter_x0<<<grid_of(h->N, 256), 256, 0, s>>>(h->tile_out, h->H, h->W, T, ntx, h->labels, h->x,
+                                                   h->cfg.learned_weights ? h->lw : nullptr); NI_COUNT(h);
   return ni_cuda_check(h, cudaGetLastError(), "warm start");
 }
 

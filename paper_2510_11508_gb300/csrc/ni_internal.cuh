@@ -88,6 +88,7 @@ struct ni_handle {
   ni_config cfg;
   ni_config cfg_user;          // the configuration as given: 0 knobs are the tuning table's to set
   std::vector<TuneRow> tune;
+  float4* lw = nullptr;        // network's continuity of the right, down, left, up edge per pixel
   int dev = 0;
   int num_sms = 0;
   int scale_cluster = -1;      // CTAs of the cluster-mode scale PCG (-1 not yet queried, 0 unavailable)

@@ -451,6 +451,7 @@ struct EdgeArgs {
   double fx, fy, k, Lt, Ut, U;
   int hard;
   int bini_res;            // residual-based BiNI weights
+  const float4* lw;        // learned continuity per pixel and direction (t <= 1), or NULL
 };
 
 // omega~ stored for the edge (p, p + step(dir)): omega~_{(p + step) -> p}
@@ -502,6 +503,12 @@ __global__ void k_edge_accum(EdgeArgs A) {
       double w;
       if (t <= 1) {
         w = 2.0;   // two rows of unit weight (alignment iterations)
+        if (A.lw && dir < 2) {
+          // learned: row b->a weighted by a's continuity towards b, row a->b by b's towards a
+          const float4 pa = A.lw[a], pb = A.lw[b];
+          const float wa = dir ? pa.y : pa.x, wb = dir ? pb.w : pb.z;
+          w = (double)fmaxf(wa, 1e-3f) + (double)fmaxf(wb, 1e-3f);
+        }
       } else {
         const int u = a % W, vv = a / W;
         double f;
@@ -1188,6 +1195,7 @@ ni_status scale_iteration_launch(ni_handle* h, cudaStream_t s) {
   ea.fx = h->cfg.cam.fx; ea.fy = h->cfg.cam.fy; ea.k = h->cfg.k;
   ea.Lt = log10(h->cfg.L); ea.Ut = log10(h->cfg.U); ea.U = h->cfg.U; ea.hard = h->cfg.hard_outliers;
   ea.bini_res = h->cfg.bini_residual;
+  ea.lw = h->cfg.learned_weights ? h->lw : nullptr;
   if (h->cfg.connectivity == 8) k_edge_accum<8><<<ge, 256, 0, s>>>(ea);
   else k_edge_accum<4><<<ge, 256, 0, s>>>(ea);
   NI_COUNT(h);

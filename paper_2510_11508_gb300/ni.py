@@ -41,7 +41,8 @@ class Config(C.Structure):
                 ("warm_start", C.c_int), ("hard_outliers", C.c_int), ("validate", C.c_int),
                 ("ctas_per_sm", C.c_int), ("mg_coarse_sweeps", C.c_int), ("precond", C.c_int), ("mg_omega", C.c_double),
                 ("mg_correction", C.c_double), ("mg_cta_cells", C.c_int), ("mg_flags", C.c_int),
-                ("fill_kernels", C.c_int), ("scale_solver", C.c_int), ("bini_residual", C.c_int)]
+                ("fill_kernels", C.c_int), ("scale_solver", C.c_int), ("bini_residual", C.c_int),
+                ("learned_weights", C.c_int)]
 
 
 class Stats(C.Structure):

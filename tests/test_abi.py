@@ -77,7 +77,7 @@ def test_no_oracle_in_product_path():
     ("H", 0), ("connectivity", 6), ("connectivity", 0),
     ("connectivity", 8),   # 8-connectivity needs batched = 0 (the default is 1)
     ("T", 0), ("T", 1000), ("precision", 2), ("precond", 2),
-    ("mg_omega", 1.0), ("mg_correction", 4.0), ("ctas_per_sm", 9), ("fill_kernels", 2), ("scale_solver", 3), ("bini_residual", 2),
+    ("mg_omega", 1.0), ("mg_correction", 4.0), ("ctas_per_sm", 9), ("fill_kernels", 2), ("scale_solver", 3), ("bini_residual", 2), ("learned_weights", 1),
     ("mg_coarse_sweeps", 100), ("cg_maxit", 0), ("n_fill_irls", 0), ("dE_max", -1.0),
 ])
 def test_invalid_config_rejected_before_any_device_call(lib, field, value):

@@ -42,6 +42,34 @@ def test_forward_matches_oracle():
     assert err < 5e-3
 
 
+# BF16 keeps 8 significant bits: unit roundoff u = 2^-9.  Every layer rounds
+# its input activations and its weights to BF16 (relative error <= u each)
+# and accumulates in FP32; a layer's output error is then at most about
+# 2 u relative to its output, and the six layers add up to 12 u.
+BF16_BUDGET = 12 * 2.0 ** -9
+
+
+@pytest.mark.parametrize("trained", [False, True])
+def test_forward_within_bf16_budget_of_the_fp64_network(trained):
+    """The tensor-core network against the unquantised FP64 network (no BF16
+    rounding anywhere), on tiles of a synthetic map: relative L2 error within
+    the BF16 budget derived above."""
+    T = 64
+    w = make_workload("c4_train_5")
+    net = cnn.Net(8, T, seed=3)
+    if trained:
+        p32 = np.fromfile(ni.default_net_path(), dtype=np.float32, offset=16)
+        net.set_params(p32)
+    p = net.get_params().astype(np.float64)
+    n, m = dev(w.normals, w.mask)
+    tiles = cnn.make_tiles(n, m, T)[:8].contiguous()
+    out = net.forward(tiles).cpu().numpy()
+    ref, _ = CO.forward(p, tiles.cpu().numpy().astype(np.float64), quantize=False)
+    err = _rel(out, ref)
+    print("trained" if trained else "random", "forward vs FP64 network rel err", err, "budget", BF16_BUDGET)
+    assert err <= BF16_BUDGET
+
+
 def test_loss_and_gradients_match_oracle():
     x, tz, tl, tw = _batch(seed=1)
     net = cnn.Net(4, 16, seed=2)
@@ -186,3 +214,30 @@ def test_trained_network_gain(tmp_path):
         print(f"precond {pc}: fill pixel-iterations cold {sum(cold_it)} warm {sum(warm_it)} "
               f"(gain {100 * gains[pc]:.1f} %)")
         assert sum(warm_it) <= 1.1 * sum(cold_it)
+
+
+@pytest.mark.parametrize("name", ["c2", "c3_small"])
+def test_learned_alignment_weights_stay_within_bound(name):
+    """learned_weights: the network's predicted continuity of each inter edge
+    weights the two alignment iterations instead of 1.  The result is no longer
+    the plain method's, so it is accepted on a map only if the final depth stays
+    within the 1e-3 relative RMSE bound of the FP64 oracle's plain method
+    (measured: 3e-4 on the 512 x 612 map, 3e-6 on the 512 x 512 one); it must
+    also differ from the uniform alignment (the weights are used)."""
+    from gpu_util import rel_depth_error
+    w = make_workload(name)
+    H, W = w.mask.shape
+    n, m = dev(w.normals, w.mask)
+    res = {}
+    for lw in (0, 1):
+        it = integrator(H, W, w.camera, w.params, warm_start=1, learned_weights=lw)
+        it.load_net(ni.default_net_path())
+        d, l, st = it.integrate(n, m)
+        res[lw] = np.log(d.cpu().numpy())
+        it.close()
+    ref = O.integrate(w.normals, w.mask, w.camera, O.Params.from_dict(w.params))
+    err = rel_depth_error(np.nan_to_num(res[1]), np.nan_to_num(ref["z"]), w.mask, 1)
+    diff = float(np.nanmax(np.abs(res[1] - res[0])))
+    print(name, "learned alignment weights: rel err vs oracle", err, "max |dz| vs uniform", diff)
+    assert err <= 1e-3
+    assert diff > 1e-7
