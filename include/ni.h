@@ -108,11 +108,12 @@ typedef struct {
   int fill_kernels;         /* multigrid fill: 0 one kernel per pass, chunks of iterations
                                replayed from a CUDA graph; 1 (default) one persistent
                                cooperative kernel with software grid barriers */
-  int scale_solver;         /* relative-scale PCG launch: 0 (default) chosen by the number of
-                               components, 1 one thread-block cluster of up to 16 CTAs
-                               (hardware cluster barriers, reductions through distributed
-                               shared memory), 2 one CTA or a cooperative grid with
-                               software barriers */
+  int scale_solver;         /* relative-scale PCG launch: 0 (default) and 1: one thread-block
+                               cluster of up to 16 CTAs (hardware cluster barriers, reductions
+                               through distributed shared memory) where the device can schedule
+                               it; 2: one CTA or a cooperative grid over all SMs with software
+                               barriers (measured slower on every map here, kept for devices
+                               without clusters) */
   int bini_residual;        /* 1: the BiNI weights (Eqs. 4-5) compare the residuals chi of the
                                two sides instead of their raw log-depth differences, in the
                                fill sweeps after the first and in the scale loop (t >= 2);

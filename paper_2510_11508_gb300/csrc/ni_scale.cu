@@ -1142,8 +1142,6 @@ int scale_cg_grid(ni_handle* h) {
 // Cluster-mode scale PCG: CTAs of 256 threads, 16 per cluster (a non-portable
 // size) where the device can schedule that, else 8, else none.
 #define NI_SCALE_CL_THREADS NI_SCALE_THREADS
-// auto mode (scale_solver = 0) takes the cluster up to this many components
-#define NI_SCALE_CL_AUTO_K 32768
 
 static cudaLaunchConfig_t cluster_cfg(int nc, cudaLaunchAttribute* at, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -1177,9 +1175,10 @@ int scale_cluster_size(ni_handle* h) {
   return h->scale_cluster;
 }
 
+// the cluster unless the caller asks for the grid (measured faster on every map
+// here, from 885 to 26193 components) or the device cannot schedule it
 static bool use_scale_cluster(ni_handle* h) {
   if (h->cfg.scale_solver == 2) return false;
-  if (h->cfg.scale_solver == 0 && h->Kcap > NI_SCALE_CL_AUTO_K) return false;
   return scale_cluster_size(h) > 0;
 }
 
