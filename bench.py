@@ -336,6 +336,7 @@ def run_ours(args):
         kw.update(over)
         cfg = ni.config_for(H, W, w.camera, params, **kw)
         it = ni.Integrator(cfg)
+        it.load_tuning()   # the table the tuner wrote on GB300 (knobs left at 0)
         if cfg.warm_start:
             it.load_net(ni.default_net_path())
         return it
@@ -504,6 +505,7 @@ def run_ours(args):
                        "fill_preconditioner": ("multigrid V-cycle" if args.precond == 1 else "Jacobi")
                        if args.variant == "batched" else "Jacobi",
                        "warm_start": "learned (6-layer BF16 conv net)" if warm else "none",
+                       "tuning": "paper_2510_11508_gb300/tuning/gb300.txt",
                        "reductions": "fp64" if args.precision == 0 else "fp32 tree + fp64 across CTAs",
                        "theta_c_deg": params["theta_c_deg"], "T": params["T"], "dE_max": params["dE_max"],
                        "can_merge": params["can_merge"], "freq_merging": params["freq_merging"],

@@ -180,6 +180,7 @@ struct ni_handle {
   uint8_t* inc0 = nullptr;     // the same for the pixels
   GridBar* mg_bar = nullptr;   // barriers of the coarse-level passes [2 * (NI_MG_MAX_LEVELS + 1)]
   int* mg_iter = nullptr;      // per-phase multigrid solve: iteration index and done flag
+  int2* mg_tact = nullptr;     // persistent multigrid solve: active tile lists, two by iteration parity
   int fill_fallbacks = 0;      // components the Jacobi fallback re-solved in this call
   float* z = nullptr;          // preconditioned residual
 

@@ -70,7 +70,8 @@ struct MgArgs {
   double* cs;
   int* ci;
   int2* tiles;             // list of tiles with a valid pixel (tile, uniform label)
-  int* ntl;                // [0] list length, [2..3] active counts by parity
+  int2* tact;              // [2][ntiles]: tiles with an active pixel at iteration k, by parity of k
+  int* ntl;                // [0] list length, [2..3] active components, [4..5] active tiles, by parity
   DevState* st;
   int N, H, W, K, Kc, ntiles, ntx, maxit, warm, ncs, project;
   float om, sc;
@@ -516,6 +517,36 @@ __device__ void comp_book(const MgArgs& A, int k, int i0, int stride) {
 }
 
 // level-0 restriction of tile t (one level-1 cell per thread)
+__device__ __forceinline__ void tile_down0(const MgArgs& A, int t, int ul, int k);
+
+// tile_down0 for the persistent kernel, which keeps a list of the tiles still
+// active: returns (the same in every thread of the CTA) whether a pixel of the
+// tile belongs to a component active at iteration k.  A tile that is not is
+// visited once more (its level-1 cells get 0, as in tile_down0) and then left
+// out of every later pass; the active set only shrinks.
+__device__ __forceinline__ bool tile_down0_active(const MgArgs& A, int t, int ul, int k) {
+  if (ul >= 0) {
+    tile_down0(A, t, ul, k);
+    return comp_now(A, ul, k);
+  }
+  down0_tile<true>(A, t, k);
+  // mixed tile: the thread of level-1 cell (cy, cx) checks its 2 x 2 pixels
+  const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
+  const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
+  bool on = false;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const int y = 2 * cy + dy, x = 2 * cx + dx;
+      if (y < A.H && x < A.W) {
+        const int lb = A.labels[y * A.W + x];
+        on |= lb >= 0 && comp_now(A, lb, k);
+      }
+    }
+  return __syncthreads_or(on) != 0;
+}
+
 __device__ __forceinline__ void tile_down0(const MgArgs& A, int t, int ul, int k) {
   if (ul >= 0) {
     if (comp_now(A, ul, k)) {
@@ -844,6 +875,16 @@ __device__ void mg_epi_apply(const MgArgs& A, int i0, int stride) {
       BODY;                                                                      \
     }                                                                            \
   }
+// the same over a list of n tiles
+#define MG_LIST_LOOP(LIST, N, BODY)                                              \
+  {                                                                              \
+    int2 nx = blockIdx.x < (N) ? (LIST)[blockIdx.x] : make_int2(0, -2);          \
+    for (int i = blockIdx.x; i < (N); i += gridDim.x) {                          \
+      const int2 te = nx;                                                        \
+      if (i + (int)gridDim.x < (N)) nx = (LIST)[i + gridDim.x];                  \
+      BODY;                                                                      \
+    }                                                                            \
+  }
 template <bool COMP, bool ALIGNED>
 __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   __shared__ TileSmem S;
@@ -872,9 +913,20 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   for (int k = 0;; ++k) {
     const int P = k & 1, Q = P ^ 1;
     comp_book(A, k, gtid, gthr);
-    MG_TILE_LOOP(tile_down0(A, te.x, te.y, k));
+    // restriction over the tiles active at k - 1 (all at k = 0); those still
+    // active at k form the list of parity P that the later passes walk
+    int2* const cur = A.tact + (size_t)P * A.ntiles;
+    {
+      const int2* prev = k == 0 ? A.tiles : A.tact + (size_t)Q * A.ntiles;
+      const int np = k == 0 ? nt : *(volatile int*)&A.ntl[4 + Q];
+      for (int i = blockIdx.x; i < np; i += gridDim.x) {
+        const int2 te = prev[i];
+        if (tile_down0_active(A, te.x, te.y, k) && threadIdx.x == 0) cur[atomicAdd(&A.ntl[4 + P], 1)] = te;
+      }
+    }
     if (!grid_barrier(&A.st->bar, err)) return;
     if (*(volatile int*)&A.ntl[2 + P] == 0) break;
+    const int na = *(volatile int*)&A.ntl[4 + P];
     const int* actk = A.ci + (size_t)P * A.Kc;
     for (int l = 1; l < A.Lc; ++l) {
       if (blockIdx.x >= A.pd[l]) break;
@@ -888,17 +940,20 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, A.pu[l] * blockDim.x);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
-    if (gtid == 0) A.ntl[2 + Q] = 0;
+    if (gtid == 0) {
+      A.ntl[2 + Q] = 0;
+      A.ntl[4 + Q] = 0;   // the list of k - 1 is read no more: it takes the tiles of k + 1
+    }
     for (int c = gtid; c < A.K; c += gthr) {
       slot(A, MG_RR + Q)[c] = 0.0;
       slot(A, MG_SR + Q)[c] = 0.0;
     }
-    MG_TILE_LOOP((tile_up0<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_up0<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
-    MG_TILE_LOOP((tile_dir<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_dir<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
     for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
-    MG_TILE_LOOP((tile_upd<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_upd<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
   }
   for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_epi_sums(A, S, A.tiles[i].x, A.tiles[i].y);
@@ -1143,6 +1198,7 @@ static ni_status ensure_mg(ni_handle* h, cudaStream_t s) {
   al(&h->inc0, (size_t)h->Npad); al(&h->z, (size_t)h->Npad);
   al(&h->mg_bar, (size_t)2 * (NI_MG_MAX_LEVELS + 1));
   al(&h->mg_iter, (size_t)4);
+  al(&h->mg_tact, (size_t)2 * h->ntiles);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return ni_fail(h, NI_ERR_OOM, "multigrid hierarchy allocation failed");
@@ -1161,6 +1217,8 @@ void free_mg(ni_handle* h) {
   cudaFree(h->mg_b); cudaFree(h->mg_e); cudaFree(h->mg_inc); cudaFree(h->inc0); cudaFree(h->z);
   cudaFree(h->mg_bar);
   cudaFree(h->mg_iter);
+  cudaFree(h->mg_tact);
+  h->mg_tact = nullptr;
   h->mg_bar = nullptr;
   h->mg_iter = nullptr;
   h->mg_lab = nullptr; h->mg_wr = h->mg_wd = h->mg_d = h->mg_invd = h->mg_b = h->mg_e = nullptr;
@@ -1259,8 +1317,8 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   cudaMemsetAsync(h->cacc, 0, sizeof(double) * 14 * (size_t)h->Kcap, s);
   cudaMemsetAsync(h->cflag, 0, sizeof(int) * 3 * (size_t)h->Kcap, s);
   cudaMemsetAsync(&h->st->bar, 0, sizeof(GridBar), s);
-  int* ntl = h->blk;   // scan scratch is free during the fill: [0] tiles, [2..3] active counts
-  cudaMemsetAsync(ntl, 0, 4 * sizeof(int), s);
+  int* ntl = h->blk;   // scan scratch is free during the fill: [0] tiles, [2..5] active counts
+  cudaMemsetAsync(ntl, 0, 8 * sizeof(int), s);
   MgArgs a;
   a.wr = h->wr; a.wd = h->wd; a.invd = h->invd; a.rhs = h->b; a.labels = h->labels; a.tile_lab = h->tile_lab;
   a.inc0 = h->inc0;
@@ -1291,6 +1349,7 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   a.mbar = h->mg_bar;
   cudaMemsetAsync(h->mg_bar, 0, sizeof(GridBar) * 2 * (NI_MG_MAX_LEVELS + 1), s);
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
+  a.tact = h->mg_tact;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   // the multigrid PCG converges in tens to hundreds of iterations; a component
   // still above the tolerance after NI_MG_MAXIT goes to the Jacobi fallback
