@@ -195,15 +195,15 @@ __device__ __forceinline__ float restrict_block(const float* __restrict__ b, con
   return s;
 }
 
-// restriction of level f (>= 1) to level c over cells i0, i0 + stride, ...
+// restriction of level f (>= 1) to level c over cells i0, i0 + stride, ...;
+// cells of converged components (act) get 0 without reading their window
 __device__ void mg_down(const Lv& f, const Lv& c, float om, int i0, int stride, const int* act) {
   const int nc = c.H * c.W;
   for (int I = i0; I < nc; I += stride) {
     const int cy = I / c.W, cx = I - cy * c.W;
     const int lc = c.lab[I];
-    const float s = restrict_block(f.b, f.invd, f.wr, f.wd, f.inc, f.H, f.W, cy, cx, om, 0.f);
     const bool on = lc >= 0 && (act == nullptr || act[lc]);
-    c.b[I] = on ? s : 0.f;
+    c.b[I] = on ? restrict_block(f.b, f.invd, f.wr, f.wd, f.inc, f.H, f.W, cy, cx, om, 0.f) : 0.f;
   }
 }
 
@@ -237,14 +237,16 @@ __device__ __forceinline__ float prolong_cell(const float* __restrict__ b, const
   return zc[0] + om * ida * (ba - t);
 }
 
-// prolongation and post-smoothing on level f (>= 1): e_f from b_f and e_c
-__device__ void mg_up(const Lv& f, const Lv& c, float om, float sc, int i0, int stride) {
+// prolongation and post-smoothing on level f (>= 1): e_f from b_f and e_c;
+// cells of converged components (act) get 0 without reading their stencil
+// (no active cell reads them: coarse edges never join two components)
+__device__ void mg_up(const Lv& f, const Lv& c, float om, float sc, int i0, int stride, const int* act) {
   const int n = f.H * f.W;
   for (int a = i0; a < n; a += stride) {
     const int y = a / f.W, x = a - y * f.W;
     const int la = f.lab[a];
-    const float e = prolong_cell(f.b, f.invd, f.wr, f.wd, f.inc, c.e, f.H, f.W, c.W, y, x, om, sc, 0.f);
-    f.e[a] = la >= 0 ? e : 0.f;
+    const bool on = la >= 0 && (act == nullptr || act[la]);
+    f.e[a] = on ? prolong_cell(f.b, f.invd, f.wr, f.wd, f.inc, c.e, f.H, f.W, c.W, y, x, om, sc, 0.f) : 0.f;
   }
 }
 
@@ -298,7 +300,7 @@ __device__ void mg_cta_levels(const MgArgs& A, MgSmem& S, const int* act) {
   }
   __syncthreads();
   for (int l = A.L - 1; l >= A.Lc; --l) {
-    mg_up(smem_level(A, S, l), smem_level(A, S, l + 1), A.om, A.sc, threadIdx.x, blockDim.x);
+    mg_up(smem_level(A, S, l), smem_level(A, S, l + 1), A.om, A.sc, threadIdx.x, blockDim.x, act);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) g.e[i] = t.e[i];
@@ -937,7 +939,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     for (int l = A.Lc - 1; l >= 1; --l) {
       if (blockIdx.x >= A.pu[l]) continue;
       if (!grid_barrier_n(&A.mbar[NI_MG_MAX_LEVELS + 1 + l], A.pu[l], err)) return;
-      mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, A.pu[l] * blockDim.x);
+      mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, A.pu[l] * blockDim.x, actk);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
     if (gtid == 0) {
@@ -1024,7 +1026,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS) k_mgx_cta(MgArgs A, MgIter* i
 __global__ void k_mgx_up(MgArgs A, MgIter* it, int l) {
   if (mgx_skip(A, it)) return;
   mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, blockIdx.x * blockDim.x + threadIdx.x,
-        gridDim.x * blockDim.x);
+        gridDim.x * blockDim.x, A.ci + (size_t)(it->k & 1) * A.Kc);
 }
 
 template <bool COMP, bool ALIGNED>
