@@ -72,6 +72,7 @@ struct MgArgs {
   int2* tiles;             // list of tiles with a valid pixel (tile, uniform label)
   int2* tact;              // [2][ntiles]: tiles with an active pixel at iteration k, by parity of k
   int* ntl;                // [0] list length, [2..3] active components, [4..5] active tiles, by parity
+  int per;                 // coarse cells per CTA of a coarse pass
   DevState* st;
   int N, H, W, K, Kc, ntiles, ntx, maxit, warm, ncs, project;
   float om, sc;
@@ -250,6 +251,80 @@ __device__ void mg_up(const Lv& f, const Lv& c, float om, float sc, int i0, int 
   }
 }
 
+// Levels 1..NI_MG_TILE_LEVELS have cells that lie inside one 32 x 32 tile of
+// the pixel grid (a level-l cell covers 2^l x 2^l pixels), so the persistent
+// kernel restricts to and prolongates on them over the list of active tiles
+// only: (32 >> l)^2 cells of level l per tile, one cell per thread, consecutive
+// threads on consecutive cells of a tile.  A listed tile with one label (te.y
+// >= 0) holds an active component, so its cells need no activity check; in a
+// mixed tile each cell checks its label.  The window or stencil loads do not
+// wait for that check (values of cells left out are never read through a
+// nonzero weight: coarse edges never join two components).
+#define NI_MG_TILE_LEVELS 5
+// the tile-local levels that the persistent kernel walks by the tile list:
+// levels 1 and 2 (256 and 64 cells per tile), where skipping the converged
+// tiles saves the most; the smaller levels run over all their cells, on fewer
+// CTAs (measured: 374 -> 346 ms fill on the 8192^2 map, unchanged on 2048^2;
+// the list on levels 3 to 5 as well cost 2 ms on 2048^2)
+#define NI_MG_LIST_LEVELS 2
+static_assert(NI_MG_LIST_LEVELS <= NI_MG_TILE_LEVELS, "list-driven levels must be tile-local");
+static_assert(NI_TILE_W == 32 && NI_TILE_H == 32, "tile-local coarse levels assume 32 x 32 tiles");
+
+// restriction from level l into level l + 1 (<= NI_MG_TILE_LEVELS) over the n
+// listed tiles, items i0, i0 + stride, ...
+__device__ void mg_down_tiles(const MgArgs& A, int l, const int2* __restrict__ list, int n, const int* act,
+                              int i0, int stride) {
+  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+  const int sh = NI_MG_TILE_LEVELS - (l + 1);   // log2 of the cells per tile side
+  const int side = 1 << sh;
+  const long long items = (long long)n << (2 * sh);
+  for (long long i = i0; i < items; i += stride) {
+    const int2 te = list[i >> (2 * sh)];
+    const int j = (int)(i & ((1 << (2 * sh)) - 1));
+    const int ty = te.x / A.ntx, tx = te.x - ty * A.ntx;
+    const int cy = (ty << sh) + (j >> sh), cx = (tx << sh) + (j & (side - 1));
+    if (cy >= c.H || cx >= c.W) continue;
+    const int I = cy * c.W + cx;
+    const int lc = c.lab[I];
+    const float v = restrict_block(f.b, f.invd, f.wr, f.wd, f.inc, f.H, f.W, cy, cx, A.om, 0.f);
+    const bool on = lc >= 0 && (te.y >= 0 || act[lc]);
+    c.b[I] = on ? v : 0.f;
+  }
+}
+
+// CTAs of the tile-local pass on level `level`: one per A.per of its cells in
+// the na active tiles, and never fewer than `floor_n`, the CTAs of the first
+// pass beyond the list-driven levels, so that the CTAs of a coarser pass are
+// always among those of a finer one (each partial barrier then covers every
+// writer of what the next pass reads)
+__device__ __forceinline__ int mg_tile_ctas(const MgArgs& A, int na, int level, int floor_n) {
+  const long long items = (long long)na << (2 * (NI_MG_TILE_LEVELS - level));
+  const long long n = (items + A.per - 1) / A.per;
+  return (int)max((long long)floor_n, min((long long)gridDim.x, max(1LL, n)));
+}
+
+// prolongation and post-smoothing on level l (<= NI_MG_TILE_LEVELS) from l + 1
+// over the n listed tiles, items i0, i0 + stride, ...
+__device__ void mg_up_tiles(const MgArgs& A, int l, const int2* __restrict__ list, int n, const int* act,
+                            int i0, int stride) {
+  const Lv f = coarse_level(A, l), c = coarse_level(A, l + 1);
+  const int sh = NI_MG_TILE_LEVELS - l;
+  const int side = 1 << sh;
+  const long long items = (long long)n << (2 * sh);
+  for (long long i = i0; i < items; i += stride) {
+    const int2 te = list[i >> (2 * sh)];
+    const int j = (int)(i & ((1 << (2 * sh)) - 1));
+    const int ty = te.x / A.ntx, tx = te.x - ty * A.ntx;
+    const int y = (ty << sh) + (j >> sh), x = (tx << sh) + (j & (side - 1));
+    if (y >= f.H || x >= f.W) continue;
+    const int a = y * f.W + x;
+    const int la = f.lab[a];
+    const float v = prolong_cell(f.b, f.invd, f.wr, f.wd, f.inc, c.e, f.H, f.W, c.W, y, x, A.om, A.sc, 0.f);
+    const bool on = la >= 0 && (te.y >= 0 || act[la]);
+    f.e[a] = on ? v : 0.f;
+  }
+}
+
 // CTA 0, once per launch: the constant data of levels Lc..L into shared memory
 __device__ void mg_smem_load(const MgArgs& A, MgSmem& S) {
   for (int l = A.Lc; l <= A.L; ++l) {
@@ -327,7 +402,7 @@ __device__ __forceinline__ float comp_mean(const MgArgs& A, int c, int k) {
 // level-0 restriction for the tile t: each of the 256 threads owns one level-1
 // cell of the tile (16 x 16 cells)
 template <bool CHECK>
-__device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k) {
+__device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k, bool uon = true) {
   const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
   const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
   const int H1 = A.lh[1], W1 = A.lw[1];
@@ -336,7 +411,7 @@ __device__ __forceinline__ void down0_tile(const MgArgs& A, int t, int k) {
   const int lc = A.clab[A.loff[1] + I];
   const float mu = (A.project && lc >= 0) ? comp_mean(A, lc, k) : 0.f;
   const float s = restrict_block(A.r, A.invd, A.wr, A.wd, A.inc0, A.H, A.W, cy, cx, A.om, mu);
-  const bool on = lc >= 0 && (!CHECK || comp_now(A, lc, k));
+  const bool on = lc >= 0 && (CHECK ? comp_now(A, lc, k) : uon);
   A.cb[A.loff[1] + I] = on ? s : 0.f;
 }
 
@@ -551,22 +626,20 @@ __device__ __forceinline__ bool tile_down0_active(const MgArgs& A, int t, int ul
 
 __device__ __forceinline__ void tile_down0(const MgArgs& A, int t, int ul, int k) {
   if (ul >= 0) {
-    if (comp_now(A, ul, k)) {
-      down0_tile<false>(A, t, k);
-    } else {   // a converged component: its level-1 cells get 0
-      const int cy = (t / A.ntx) * (NI_TILE_H / 2) + (threadIdx.x >> 4);
-      const int cx = (t % A.ntx) * (NI_TILE_W / 2) + (threadIdx.x & 15);
-      if (cy < A.lh[1] && cx < A.lw[1]) A.cb[A.loff[1] + cy * A.lw[1] + cx] = 0.f;
-    }
+    // the window loads go out with those of the activity test; the level-1
+    // cells of a converged component get 0
+    down0_tile<false>(A, t, k, comp_now(A, ul, k));
   } else {
     down0_tile<true>(A, t, k);
   }
 }
 
 // level-0 prolongation and smoothing: z_k and r^T z per component
-template <bool COMP, bool ALIGNED>
+// LIST: t comes from the list of tiles active at k, so a tile with one label
+// holds an active component and needs no activity load
+template <bool COMP, bool ALIGNED, bool LIST = false>
 __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
-  if (ul >= 0 && !actk[ul]) return;   // uniform across the CTA
+  if (!LIST && ul >= 0 && !actk[ul]) return;   // uniform across the CTA
   const int W = A.W, H = A.H, l8 = threadIdx.x & 7, W1 = A.lw[1];
   const float om = A.om, sc = A.sc;
   const float* e1 = A.ce + A.loff[1];
@@ -577,7 +650,7 @@ __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   else ldlab<ALIGNED>(A.labels, g.a, g.nval, lab);
   bool now[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && actk[lab[j]];
+  for (int j = 0; j < 4; ++j) now[j] = lab[j] >= 0 && ((LIST && ul >= 0) || actk[lab[j]]);
   const float4 r4 = ldg<ALIGNED>(A.r, g.a, g.nval);
   const float4 id4 = ldg<ALIGNED>(A.invd, g.a, g.nval);
   float mu[4] = {0.f, 0.f, 0.f, 0.f};
@@ -664,9 +737,9 @@ __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
 }
 
 // direction: p_k = z_k + beta_k p_{k-1}; q = A p_k; p^T A p per component
-template <bool COMP, bool ALIGNED>
+template <bool COMP, bool ALIGNED, bool LIST = false>
 __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
-  if (ul >= 0 && !actk[ul]) return;
+  if (!LIST && ul >= 0 && !actk[ul]) return;
   const int W = A.W, H = A.H, l8 = threadIdx.x & 7, Kc = A.Kc;
   const int P = k & 1, Q = P ^ 1;
   const float* pold = Q ? A.pb1 : A.pb0;
@@ -694,7 +767,7 @@ __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   if (ul >= 0) {   // one component: lane 0 of each warp computes beta, no CTA barrier
     float bt = (threadIdx.x & 31) == 0 ? betaf(ul) : 0.f;
     bt = __shfl_sync(NI_FULL, bt, 0);
-    const bool on = actk[ul] != 0;
+    const bool on = LIST || actk[ul] != 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       now[j] = lab[j] >= 0 && on;
@@ -757,9 +830,9 @@ __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
 }
 
 // update: alpha_k; x += alpha p; r = (r - mean) - alpha q; r^T r, sum r per component
-template <bool COMP, bool ALIGNED>
+template <bool COMP, bool ALIGNED, bool LIST = false>
 __device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
-  if (ul >= 0 && !actk[ul]) return;
+  if (!LIST && ul >= 0 && !actk[ul]) return;
   const int P = k & 1, Q = P ^ 1;
   const float* pnew = P ? A.pb1 : A.pb0;
   const double* rz = slot(A, MG_RZ + P);
@@ -795,7 +868,7 @@ __device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   bool now[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    now[j] = lab[j] >= 0 && actk[lab[j]];
+    now[j] = lab[j] >= 0 && ((LIST && ul >= 0) || actk[lab[j]]);
     float al = 0.f, mu = 0.f;
     if (now[j]) {
       if (ul >= 0) {
@@ -866,18 +939,9 @@ __device__ void mg_epi_apply(const MgArgs& A, int i0, int stride) {
 // ---------------------------------------------------------------------------
 // persistent variant: one cooperative launch, grid barriers between phases
 // ---------------------------------------------------------------------------
-// the CTA's tiles of the list; the next entry is loaded before the current tile
-// is processed, so its latency hides behind the tile's work
-#define MG_TILE_LOOP(BODY)                                                       \
-  {                                                                              \
-    int2 nx = blockIdx.x < nt ? A.tiles[blockIdx.x] : make_int2(0, -2);          \
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) {                           \
-      const int2 te = nx;                                                        \
-      if (i + (int)gridDim.x < nt) nx = A.tiles[i + gridDim.x];                  \
-      BODY;                                                                      \
-    }                                                                            \
-  }
-// the same over a list of n tiles
+// the CTA's tiles of a list of n tiles (i = blockIdx.x, + gridDim.x, ...); the
+// next entry is loaded before the current tile is processed, so its latency
+// hides behind the tile's work
 #define MG_LIST_LOOP(LIST, N, BODY)                                              \
   {                                                                              \
     int2 nx = blockIdx.x < (N) ? (LIST)[blockIdx.x] : make_int2(0, -2);          \
@@ -909,7 +973,7 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
   if (A.warm) {
     comp_warm_alpha(A, gtid, gthr);
     if (!grid_barrier(&A.st->bar, err)) return;
-    for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_warm<COMP, ALIGNED>(A, S, A.tiles[i].x, A.tiles[i].y);
+    MG_LIST_LOOP(A.tiles, nt, (tile_warm<COMP, ALIGNED>(A, S, te.x, te.y)));
     if (!grid_barrier(&A.st->bar, err)) return;
   }
   for (int k = 0;; ++k) {
@@ -921,25 +985,34 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
     {
       const int2* prev = k == 0 ? A.tiles : A.tact + (size_t)Q * A.ntiles;
       const int np = k == 0 ? nt : *(volatile int*)&A.ntl[4 + Q];
-      for (int i = blockIdx.x; i < np; i += gridDim.x) {
-        const int2 te = prev[i];
+      MG_LIST_LOOP(prev, np, {
         if (tile_down0_active(A, te.x, te.y, k) && threadIdx.x == 0) cur[atomicAdd(&A.ntl[4 + P], 1)] = te;
-      }
+      });
     }
     if (!grid_barrier(&A.st->bar, err)) return;
     if (*(volatile int*)&A.ntl[2 + P] == 0) break;
     const int na = *(volatile int*)&A.ntl[4 + P];
     const int* actk = A.ci + (size_t)P * A.Kc;
+    // coarse levels: a pass on level l runs on the first n CTAs and ends with a
+    // barrier among them; n does not grow towards coarser levels
+    const int tail_d = NI_MG_LIST_LEVELS < A.Lc ? A.pd[NI_MG_LIST_LEVELS] : 1;
     for (int l = 1; l < A.Lc; ++l) {
-      if (blockIdx.x >= A.pd[l]) break;
-      mg_down(coarse_level(A, l), coarse_level(A, l + 1), A.om, gtid, A.pd[l] * blockDim.x, actk);
-      if (!grid_barrier_n(&A.mbar[l], A.pd[l], err)) return;
+      const bool tl = l + 1 <= NI_MG_LIST_LEVELS;
+      const int n = tl ? mg_tile_ctas(A, na, l + 1, tail_d) : A.pd[l];
+      if (blockIdx.x >= n) break;
+      if (tl) mg_down_tiles(A, l, cur, na, actk, gtid, n * blockDim.x);
+      else mg_down(coarse_level(A, l), coarse_level(A, l + 1), A.om, gtid, n * blockDim.x, actk);
+      if (!grid_barrier_n(&A.mbar[l], n, err)) return;
     }
     if (blockIdx.x == 0) mg_cta_levels(A, s_mg, actk);
+    const int tail_u = NI_MG_LIST_LEVELS + 1 < A.Lc ? A.pu[NI_MG_LIST_LEVELS + 1] : 1;
     for (int l = A.Lc - 1; l >= 1; --l) {
-      if (blockIdx.x >= A.pu[l]) continue;
-      if (!grid_barrier_n(&A.mbar[NI_MG_MAX_LEVELS + 1 + l], A.pu[l], err)) return;
-      mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, A.pu[l] * blockDim.x, actk);
+      const bool tl = l <= NI_MG_LIST_LEVELS;
+      const int n = tl ? mg_tile_ctas(A, na, l, tail_u) : A.pu[l];
+      if (blockIdx.x >= n) continue;
+      if (!grid_barrier_n(&A.mbar[NI_MG_MAX_LEVELS + 1 + l], n, err)) return;
+      if (tl) mg_up_tiles(A, l, cur, na, actk, gtid, n * blockDim.x);
+      else mg_up(coarse_level(A, l), coarse_level(A, l + 1), A.om, A.sc, gtid, n * blockDim.x, actk);
     }
     if (!grid_barrier(&A.st->bar, err)) return;
     if (gtid == 0) {
@@ -950,15 +1023,15 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       slot(A, MG_RR + Q)[c] = 0.0;
       slot(A, MG_SR + Q)[c] = 0.0;
     }
-    MG_LIST_LOOP(cur, na, (tile_up0<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_up0<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
-    MG_LIST_LOOP(cur, na, (tile_dir<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_dir<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
     for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
-    MG_LIST_LOOP(cur, na, (tile_upd<COMP, ALIGNED>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_upd<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
     if (!grid_barrier(&A.st->bar, err)) return;
   }
-  for (int i = blockIdx.x; i < nt; i += gridDim.x) tile_epi_sums(A, S, A.tiles[i].x, A.tiles[i].y);
+  MG_LIST_LOOP(A.tiles, nt, (tile_epi_sums(A, S, te.x, te.y)));
   if (!grid_barrier(&A.st->bar, err)) return;
   mg_epi_apply(A, gtid, gthr);
 }
@@ -1343,7 +1416,7 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
     a.smo[l] = 0;
     if (l >= Lc && l <= L) { a.smo[l] = so; so += (int)cells(l); }
     a.pd[l] = a.pu[l] = grid;
-    if (l >= 1 && l < Lc) {
+    if (l >= 1 && l < Lc) {   // the tile-local levels size their passes on the device
       a.pd[l] = (int)std::max(1LL, std::min((long long)grid, (cells(l + 1) + per_cta - 1) / per_cta));
       a.pu[l] = (int)std::max(1LL, std::min((long long)grid, (cells(l) + per_cta - 1) / per_cta));
     }
@@ -1352,6 +1425,7 @@ ni_status mg_solve_launch(ni_handle* h, cudaStream_t s) {
   cudaMemsetAsync(h->mg_bar, 0, sizeof(GridBar) * 2 * (NI_MG_MAX_LEVELS + 1), s);
   a.cs = h->cacc; a.ci = h->cflag; a.tiles = reinterpret_cast<int2*>(h->tiles); a.ntl = ntl; a.st = h->st;
   a.tact = h->mg_tact;
+  a.per = (int)per_cta;
   a.N = h->N; a.H = h->H; a.W = h->W; a.K = h->K_host; a.Kc = h->Kcap; a.ntiles = h->ntiles; a.ntx = h->ntx;
   // the multigrid PCG converges in tens to hundreds of iterations; a component
   // still above the tolerance after NI_MG_MAXIT goes to the Jacobi fallback

@@ -80,6 +80,21 @@ __device__ __forceinline__ float2 warp_total(float v) {
   return make_float2(warp_sum_f(v), 0.f);
 }
 
+// Add `t` to the CTA's shared table entry of label `key` (linear probing over
+// TAB_SLOTS slots); straight to dst[j] + key when the table is full.
+template <int NV>
+__device__ __forceinline__ void table_add(int key, int j, double t, double* const (&dst)[NV], int* s_key,
+                                          double* s_val) {
+  int h = key & (TAB_SLOTS - 1), slot = -1;
+  for (int probe = 0; probe < TAB_SLOTS; ++probe) {
+    const int old = atomicCAS(&s_key[h], -1, key);
+    if (old == -1 || old == key) { slot = h; break; }
+    h = (h + 1) & (TAB_SLOTS - 1);
+  }
+  if (slot >= 0) atomicAdd(&s_val[slot * 3 + j], t);
+  else atomicAdd(dst[j] + key, t);
+}
+
 // Add NV per-thread values into dst[v][label].  `key` is the label all of the
 // thread's contributing pixels share (-1: nothing to add; threads with pixels of
 // several labels add per pixel before calling, and pass -1).  ul >= 0: the whole
@@ -97,9 +112,12 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
 #pragma unroll
       for (int j = 0; j < NV; ++j) sh[wid * NV + j] = (double)w[j].x + (double)w[j].y;
     __syncthreads();
-    if (threadIdx.x < NV) {
-      double t = 0.0;
-      for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) t += sh[ww * NV + threadIdx.x];
+    if (threadIdx.x < NV) {   // pairwise over the (at most 8) warps: 3 dependent FP64 adds, not 7
+      const int nw = (int)(blockDim.x >> 5);
+      double u[8];
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) u[ww] = ww < nw ? sh[ww * NV + threadIdx.x] : 0.0;
+      const double t = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7]));
       if (t != 0.0) atomicAdd(dst[threadIdx.x] + ul, t);
     }
     __syncthreads();
@@ -128,18 +146,10 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
     acc[j] = make_float2(hi, lo);
   }
   if (tail && key >= 0) {
-    int h = key & (TAB_SLOTS - 1), slot = -1;
-    for (int probe = 0; probe < TAB_SLOTS; ++probe) {
-      const int old = atomicCAS(&s_key[h], -1, key);
-      if (old == -1 || old == key) { slot = h; break; }
-      h = (h + 1) & (TAB_SLOTS - 1);
-    }
 #pragma unroll
     for (int j = 0; j < NV; ++j) {
       const double t = (double)acc[j].x + (double)acc[j].y;
-      if (t == 0.0) continue;
-      if (slot >= 0) atomicAdd(&s_val[slot * 3 + j], t);
-      else atomicAdd(dst[j] + key, t);
+      if (t != 0.0) table_add<NV>(key, j, t, dst, s_key, s_val);
     }
   }
   __syncthreads();
