@@ -638,7 +638,8 @@ __device__ __forceinline__ void tile_down0(const MgArgs& A, int t, int ul, int k
 // LIST: t comes from the list of tiles active at k, so a tile with one label
 // holds an active component and needs no activity load
 template <bool COMP, bool ALIGNED, bool LIST = false>
-__device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+__device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk,
+                         int par = -1) {
   if (!LIST && ul >= 0 && !actk[ul]) return;   // uniform across the CTA
   const int W = A.W, H = A.H, l8 = threadIdx.x & 7, W1 = A.lw[1];
   const float om = A.om, sc = A.sc;
@@ -733,12 +734,13 @@ __device__ void tile_up0(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   const int key = ul >= 0 ? ul : group_key(lab, now);
   float v[1];
   group_values<1>(key, lab, now, pv, dst, v);
-  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh, par);
 }
 
 // direction: p_k = z_k + beta_k p_{k-1}; q = A p_k; p^T A p per component
 template <bool COMP, bool ALIGNED, bool LIST = false>
-__device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+__device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk,
+                         int par = -1) {
   if (!LIST && ul >= 0 && !actk[ul]) return;
   const int W = A.W, H = A.H, l8 = threadIdx.x & 7, Kc = A.Kc;
   const int P = k & 1, Q = P ^ 1;
@@ -826,12 +828,13 @@ __device__ void tile_dir(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   const int key = ul >= 0 ? ul : group_key(lab, now);
   float v[1];
   group_values<1>(key, lab, now, pv, dst, v);
-  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+  tile_accum<COMP, 1>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh, par);
 }
 
 // update: alpha_k; x += alpha p; r = (r - mean) - alpha q; r^T r, sum r per component
 template <bool COMP, bool ALIGNED, bool LIST = false>
-__device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk) {
+__device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, const int* actk,
+                         int par = -1) {
   if (!LIST && ul >= 0 && !actk[ul]) return;
   const int P = k & 1, Q = P ^ 1;
   const float* pnew = P ? A.pb1 : A.pb0;
@@ -896,7 +899,7 @@ __device__ void tile_upd(const MgArgs& A, TileSmem& S, int t, int ul, int k, con
   const int key = ul >= 0 ? ul : group_key(lab, now);
   float v[2];
   group_values<2>(key, lab, now, pv, dst, v);
-  tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh);
+  tile_accum<COMP, 2>(ul, key == -2 ? -1 : key, v, dst, S.key, S.val, S.sh, par);
 }
 
 // epilogue, first part: sum of x and pixel count per component
@@ -945,11 +948,13 @@ __device__ void mg_epi_apply(const MgArgs& A, int i0, int stride) {
 #define MG_LIST_LOOP(LIST, N, BODY)                                              \
   {                                                                              \
     int2 nx = blockIdx.x < (N) ? (LIST)[blockIdx.x] : make_int2(0, -2);          \
-    for (int i = blockIdx.x; i < (N); i += gridDim.x) {                          \
+    int tpar = 0;   /* parity of the CTA's tile step */                          \
+    for (int i = blockIdx.x; i < (N); i += gridDim.x, tpar ^= 1) {               \
       const int2 te = nx;                                                        \
       if (i + (int)gridDim.x < (N)) nx = (LIST)[i + gridDim.x];                  \
       BODY;                                                                      \
     }                                                                            \
+    (void)tpar;                                                                  \
   }
 template <bool COMP, bool ALIGNED>
 __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
@@ -1023,12 +1028,12 @@ __global__ void __launch_bounds__(NI_TILE_THREADS, 4) k_pcg_mg(MgArgs A) {
       slot(A, MG_RR + Q)[c] = 0.0;
       slot(A, MG_SR + Q)[c] = 0.0;
     }
-    MG_LIST_LOOP(cur, na, (tile_up0<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_up0<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk, tpar)));
     if (!grid_barrier(&A.st->bar, err)) return;
-    MG_LIST_LOOP(cur, na, (tile_dir<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_dir<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk, tpar)));
     if (!grid_barrier(&A.st->bar, err)) return;
     for (int c = gtid; c < A.K; c += gthr) slot(A, MG_RZ + Q)[c] = 0.0;
-    MG_LIST_LOOP(cur, na, (tile_upd<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk)));
+    MG_LIST_LOOP(cur, na, (tile_upd<COMP, ALIGNED, true>(A, S, te.x, te.y, k, actk, tpar)));
     if (!grid_barrier(&A.st->bar, err)) return;
   }
   MG_LIST_LOOP(A.tiles, nt, (tile_epi_sums(A, S, te.x, te.y)));

@@ -100,14 +100,19 @@ __device__ __forceinline__ void table_add(int key, int j, double t, double* cons
 // several labels add per pixel before calling, and pass -1).  ul >= 0: the whole
 // tile is one component.  Warp trees in float (float-float when COMP), the
 // per-warp totals in double.  All threads of the CTA call it.
+// par = 0 or 1 (the parity of the caller's tile step; 16 * NV doubles of sh):
+// a one-label tile's warp totals go to half `par` of sh, so the next tile, which
+// writes the other half, needs no second CTA barrier to wait for the adding
+// thread; par = -1: one half and two barriers.
 template <bool COMP, int NV>
 __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV], double* const (&dst)[NV],
-                                           int* s_key, double* s_val, double* sh) {
+                                           int* s_key, double* s_val, double* sh, int par = -1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (ul >= 0) {
     float2 w[NV];
 #pragma unroll
     for (int j = 0; j < NV; ++j) w[j] = warp_total<COMP>(v[j]);
+    if (par > 0) sh += 8 * NV;
     if (lane == 0)
 #pragma unroll
       for (int j = 0; j < NV; ++j) sh[wid * NV + j] = (double)w[j].x + (double)w[j].y;
@@ -120,7 +125,7 @@ __device__ __forceinline__ void tile_accum(int ul, int key, const float (&v)[NV]
       const double t = ((u[0] + u[1]) + (u[2] + u[3])) + ((u[4] + u[5]) + (u[6] + u[7]));
       if (t != 0.0) atomicAdd(dst[threadIdx.x] + ul, t);
     }
-    __syncthreads();
+    if (par < 0) __syncthreads();
     return;
   }
   // warp-segmented runs of equal keys
