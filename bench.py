@@ -281,10 +281,14 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_per_px_iter(kernel, source):
+def traffic_per_px_iter(kernel, source, npx):
     """DRAM bytes per active pixel-iteration of a fill kernel from the committed
     ncu summary profiles/<kernel>_traffic.json, if it was taken on the current
-    kernel source."""
+    kernel source.  The file holds captures of several maps ("captures": grid
+    pixels -> bytes per pixel-iteration); a map uses the capture of the largest
+    captured map not larger than itself (the smallest capture if none is): the
+    figure depends on how much of the arrays the L2 holds, so it is carried
+    only towards larger maps.  Returns (bytes, captured map) or (None, None)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     src = os.path.join(ROOT, "paper_2510_11508_gb300", "csrc", source)
@@ -292,10 +296,15 @@ def traffic_per_px_iter(kernel, source):
         d = json.load(open(p))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if d.get("source_sha256") != h:
-            return None
-        return float(d["dram_bytes_per_px_iter"])
+            return None, None
+        caps = sorted(d["captures"].values(), key=lambda c: c["grid_px"])
+        best = caps[0]
+        for c in caps:
+            if c["grid_px"] <= npx:
+                best = c
+        return float(best["dram_bytes_per_px_iter"]), best["workload"]
     except Exception:
-        return None
+        return None, None
 
 
 # ---------------------------------------------------------------------------
@@ -494,11 +503,12 @@ def run_ours(args):
     alg_bytes = ALG_BYTES_PER_PX_ITER * units
     achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     built = bpp * units / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
-    tpi = traffic_per_px_iter(kernel, source)
+    tpi, tmap = traffic_per_px_iter(kernel, source, H * W)
     roof = {"kernel": kernel,
             "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
             "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
             "traffic": (tpi * units) if tpi is not None else None,
+            "traffic_from": tmap,
             "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_px_iter": ALG_BYTES_PER_PX_ITER,
             "px_iters_per_launch": units, "ms_per_launch": per_launch_ms,
             "kernel_bytes_per_px_iter": bpp, "kernel_achieved": built,
