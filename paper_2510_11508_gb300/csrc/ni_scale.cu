@@ -930,8 +930,12 @@ __device__ __forceinline__ void spmv_rows(const RowSlice& RS, UJ uj, ROW row, do
 //     u) and then w = L u with the inner products, a cluster barrier between.
 // Thread 0 turns the sums into the scalars (two independent divisions an
 // iteration) and broadcasts them.
+// threads of a cluster-mode CTA: each thread owns about K / (16 x 512) rows, so
+// fewer of its rows' dependent loads (L2 gathers of the neighbours' u) queue
+// behind one another than with 256
+#define NI_SCALE_CL_THREADS 512
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) k_scale_cg(ScaleArgs A) {
+__global__ void __launch_bounds__(MODE == 1 ? NI_SCALE_CL_THREADS : 256, 1) k_scale_cg(ScaleArgs A) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ RedShared R;
   __shared__ double sc[4];   // alpha, beta, done
@@ -1139,9 +1143,8 @@ int scale_cg_grid(ni_handle* h) {
   return std::max(1, std::min(h->num_sms, need));
 }
 
-// Cluster-mode scale PCG: CTAs of 256 threads, 16 per cluster (a non-portable
+// Cluster-mode scale PCG: CTAs of NI_SCALE_CL_THREADS threads, 16 per cluster (a non-portable
 // size) where the device can schedule that, else 8, else none.
-#define NI_SCALE_CL_THREADS NI_SCALE_THREADS
 
 static cudaLaunchConfig_t cluster_cfg(int nc, cudaLaunchAttribute* at, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
